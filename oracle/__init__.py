@@ -61,7 +61,7 @@ def lib():
             L.or_gs_ratio.restype = ctypes.c_double
             L.or_gs_ratio.argtypes = [ctypes.c_double, ctypes.c_int, _dp, _dp]
             L.or_integrals_1d.restype = None
-            L.or_integrals_1d.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+            L.or_integrals_1d.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
             L.or_axis_tables.restype = None
             L.or_axis_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
             L.or_multiplier.restype = ctypes.c_int
@@ -143,11 +143,11 @@ def gs_ratio(r: float, w: np.ndarray, a: np.ndarray) -> float:
 
 
 # --------------------------------------------------------------------------- 1D integrals
-def integrals_1d(alpha: float, L: float, kappa: float):
-    """(G, H) of eq. (Gten_sep) for one (alpha, kappa) by adaptive Gauss-Kronrod."""
+def integrals_1d(alpha: float, L: float, k: int):
+    """(G, H) of eq. (Gten_sep) at kappa = pi k / L by adaptive Gauss-Kronrod."""
     G = ctypes.c_double()
     H = ctypes.c_double()
-    lib().or_integrals_1d(float(alpha), float(L), float(kappa), ctypes.byref(G), ctypes.byref(H))
+    lib().or_integrals_1d(float(alpha), float(L), int(k), ctypes.byref(G), ctypes.byref(H))
     return G.value, H.value
 
 

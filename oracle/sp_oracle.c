@@ -127,9 +127,33 @@ static const double or_wg7[4] = { /* weights of the Gauss nodes xk15[1], [3], [5
     0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
     0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
 
-/* Apply the G7/K15 pair to f(y) = y^m exp(-alpha y^2) cos(kappa y), m in {0, 2}, on [lo, hi].
-   abs15 receives the K15 rule applied to |f| (the size that rounding acts on). */
-static void or_gk15(double alpha, double kappa, double lo, double hi,
+/*
+ * Integrands on [0, L], each a polynomial in y times exp(-alpha y^2), multiplied by
+ * cos(kappa y):
+ *   DIRECT:  f = exp(-a y^2)  and  g = y^2 exp(-a y^2)
+ *   FOURTH:  the fourth derivatives
+ *            f4 = (16a^4y^4 - 48a^3y^2 + 12a^2) exp(-a y^2)
+ *            g4 = (16a^4y^6 - 112a^3y^4 + 156a^2y^2 - 24a) exp(-a y^2)
+ */
+enum { OR_DIRECT = 0, OR_FOURTH = 1 };
+
+static void or_integrand(int which, double alpha, double y, double* p0, double* p2)
+{
+    double e = exp(-alpha * y * y);
+    double y2 = y * y;
+    if (which == OR_DIRECT) {
+        *p0 = e;
+        *p2 = y2 * e;
+    } else {
+        double a2 = alpha * alpha, a3 = a2 * alpha, a4 = a3 * alpha;
+        *p0 = (16.0 * a4 * y2 * y2 - 48.0 * a3 * y2 + 12.0 * a2) * e;
+        *p2 = (16.0 * a4 * y2 * y2 * y2 - 112.0 * a3 * y2 * y2 + 156.0 * a2 * y2 - 24.0 * alpha) * e;
+    }
+}
+
+/* Apply the G7/K15 pair to both integrands (times cos(kappa y)) on [lo, hi].
+   abs15 receives the K15 rule applied to their absolute values. */
+static void or_gk15(int which, double alpha, double kappa, double lo, double hi,
                     double k15[2], double g7[2], double abs15[2])
 {
     double c = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
@@ -138,12 +162,14 @@ static void or_gk15(double alpha, double kappa, double lo, double hi,
         int npts = (i == 7) ? 1 : 2;
         for (int sgn = 0; sgn < npts; ++sgn) {
             double y = (sgn == 0) ? c + hw * or_xk15[i] : c - hw * or_xk15[i];
-            double f0 = exp(-alpha * y * y) * cos(kappa * y);
-            double f2 = y * y * f0;
+            double p0, p2;
+            or_integrand(which, alpha, y, &p0, &p2);
+            double cs = cos(kappa * y);
+            double f0 = p0 * cs, f2 = p2 * cs;
             k15[0] += or_wk15[i] * f0;
             k15[1] += or_wk15[i] * f2;
-            abs15[0] += or_wk15[i] * fabs(f0);
-            abs15[1] += or_wk15[i] * fabs(f2);
+            abs15[0] += or_wk15[i] * fabs(p0);
+            abs15[1] += or_wk15[i] * fabs(p2);
             if (i & 1) {
                 g7[0] += or_wg7[i >> 1] * f0;
                 g7[1] += or_wg7[i >> 1] * f2;
@@ -162,11 +188,11 @@ static void or_gk15(double alpha, double kappa, double lo, double hi,
  * difference is already at the rounding level of its own sum is accepted too,
  * and bisection stops at depth 30.
  */
-static void or_gk_adapt(double alpha, double kappa, double lo, double hi,
+static void or_gk_adapt(int which, double alpha, double kappa, double lo, double hi,
                         double tol0, double tol2, int depth, double out[2])
 {
     double k15[2], g7[2], ab[2];
-    or_gk15(alpha, kappa, lo, hi, k15, g7, ab);
+    or_gk15(which, alpha, kappa, lo, hi, k15, g7, ab);
     double e0 = fabs(k15[0] - g7[0]), e2 = fabs(k15[1] - g7[1]);
     int ok0 = e0 <= tol0 || e0 <= 50.0 * DBL_EPSILON * ab[0];
     int ok2 = e2 <= tol2 || e2 <= 50.0 * DBL_EPSILON * ab[1];
@@ -176,52 +202,92 @@ static void or_gk_adapt(double alpha, double kappa, double lo, double hi,
         return;
     }
     double mid = 0.5 * (lo + hi);
-    or_gk_adapt(alpha, kappa, lo, mid, 0.5 * tol0, 0.5 * tol2, depth + 1, out);
-    or_gk_adapt(alpha, kappa, mid, hi, 0.5 * tol0, 0.5 * tol2, depth + 1, out);
+    or_gk_adapt(which, alpha, kappa, lo, mid, 0.5 * tol0, 0.5 * tol2, depth + 1, out);
+    or_gk_adapt(which, alpha, kappa, mid, hi, 0.5 * tol0, 0.5 * tol2, depth + 1, out);
 }
 
 /*
- * The tolerance is relative to the size of the non-oscillating integrand on
- * [0, L] (the kappa = 0 integral, which bounds |G| and |H|), because G and H
- * themselves can cancel to zero at kappa > 0.
- *
- * Bisection starts from a plain initial partition, so that no first panel can
- * miss the integrand: breakpoints at 0, w, 2w, 4w, ... (w = 1/sqrt(alpha), the
- * width of the Gaussian, when it is below L/2), and each piece cut into equal
- * parts no longer than half a period of cos(kappa y).
+ * int_0^L P(y) cos(kappa y) dy for both integrands of `which`, by adaptive G7/K15
+ * started from a plain initial partition, so that no first panel can miss the
+ * integrand: breakpoints at 0, w, 2w, 4w, ... (w = 1/sqrt(alpha), the width of the
+ * Gaussian, when it is below L/2), and each piece cut into equal parts no longer
+ * than half a period of cos(kappa y).  The tolerance is relative to the integral of
+ * |P| over [0, L] (estimated on that partition), because the oscillating integral
+ * itself can cancel to far below it.
  */
-void or_integrals_1d(double alpha, double L, double kappa, double* G, double* H)
+#define OR_MAX_PIECES 8192
+static void or_quad(int which, double alpha, double L, double kappa, double out[2])
 {
     const double rel = 1e-14;
     double sa = sqrt(alpha);
-    double m0, m2;  /* int_0^L exp(-a y^2) dy  and  int_0^L y^2 exp(-a y^2) dy */
-    if (sa * L < 1e-6) {  /* exp(-a y^2) = 1 to working precision */
-        m0 = L;
-        m2 = L * L * L / 3.0;
-    } else {
-        m0 = 0.5 * sqrt(OR_PI) / sa * erf(sa * L);
-        m2 = 0.25 * sqrt(OR_PI) / (alpha * sa) * erf(sa * L) - 0.5 * L * exp(-alpha * L * L) / alpha;
-    }
     double bp[80];
     int nb = 0;
     bp[nb++] = 0.0;
     double wdt = (sa > 0.0) ? 1.0 / sa : L;
     for (double b = wdt; b < 0.5 * L && nb < 70; b *= 2.0) bp[nb++] = b;
     bp[nb++] = L;
-    double out[2] = {0.0, 0.0};
+    static _Thread_local double lo_[OR_MAX_PIECES], hi_[OR_MAX_PIECES];
+    int np = 0;
     for (int i = 0; i + 1 < nb; ++i) {
         double len = bp[i + 1] - bp[i];
         int parts = (int)ceil(len * fabs(kappa) / OR_PI);
         if (parts < 1) parts = 1;
-        for (int j = 0; j < parts; ++j) {
-            double lo = bp[i] + len * j / parts;
-            double hi = (j + 1 == parts) ? bp[i + 1] : bp[i] + len * (j + 1) / parts;
-            double share = (hi - lo) / L;
-            or_gk_adapt(alpha, kappa, lo, hi, rel * m0 * share, rel * m2 * share, 0, out);
+        for (int j = 0; j < parts && np < OR_MAX_PIECES; ++j) {
+            lo_[np] = bp[i] + len * j / parts;
+            hi_[np] = (j + 1 == parts) ? bp[i + 1] : bp[i] + len * (j + 1) / parts;
+            ++np;
         }
     }
-    *G = 2.0 * out[0];
-    *H = 2.0 * out[1];
+    double scale[2] = {0.0, 0.0};
+    for (int i = 0; i < np; ++i) {
+        double k15[2], g7[2], ab[2];
+        or_gk15(which, alpha, kappa, lo_[i], hi_[i], k15, g7, ab);
+        scale[0] += ab[0];
+        scale[1] += ab[1];
+    }
+    out[0] = out[1] = 0.0;
+    for (int i = 0; i < np; ++i) {
+        double share = (hi_[i] - lo_[i]) / L;
+        or_gk_adapt(which, alpha, kappa, lo_[i], hi_[i], rel * scale[0] * share, rel * scale[1] * share, 0, out);
+    }
+}
+
+/*
+ * G and H of eq. (Gten_sep) at wavenumber index k (kappa = pi k / L).
+ *
+ * For kappa^2 < 4 alpha (and k = 0) the integrals are taken directly.  Above, where G
+ * and H are small next to the size of their integrands, they are taken in the form
+ * that two integrations by parts give.  With kappa L = pi k, sin(kappa L) = 0 and
+ * cos(kappa L) = (-1)^k, and f, g are even so their first and third derivatives
+ * vanish at 0:
+ *     int_0^L f cos(kappa y) dy = (-1)^k [ f1(L)/kappa^2 - f3(L)/kappa^4 ]
+ *                                 + (1/kappa^4) int_0^L f4(y) cos(kappa y) dy
+ * (f1, f3, f4: first, third, fourth derivative), which carries the boundary terms
+ * exactly and leaves a remainder whose quadrature error is relative to the (small)
+ * result.  Both forms are exact identities.
+ */
+void or_integrals_1d(double alpha, double L, int k, double* G, double* H)
+{
+    double kappa = OR_PI * (double)k / L;
+    double out[2];
+    if (k == 0 || kappa * kappa < 4.0 * alpha) {
+        or_quad(OR_DIRECT, alpha, L, kappa, out);
+        *G = 2.0 * out[0];
+        *H = 2.0 * out[1];
+        return;
+    }
+    double e = exp(-alpha * L * L);
+    double a2 = alpha * alpha, a3 = a2 * alpha;
+    double L2 = L * L;
+    double f1 = -2.0 * alpha * L * e;                                                    /* f'(L)   */
+    double f3 = (-8.0 * a3 * L2 * L + 12.0 * a2 * L) * e;                                /* f'''(L) */
+    double g1 = (2.0 * L - 2.0 * alpha * L2 * L) * e;                                    /* g'(L)   */
+    double g3 = (-24.0 * alpha * L + 36.0 * a2 * L2 * L - 8.0 * a3 * L2 * L2 * L) * e;   /* g'''(L) */
+    double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+    double k2 = kappa * kappa, k4 = k2 * k2;
+    or_quad(OR_FOURTH, alpha, L, kappa, out);
+    *G = 2.0 * (sgn * (f1 / k2 - f3 / k4) + out[0] / k4);
+    *H = 2.0 * (sgn * (g1 / k2 - g3 / k4) + out[1] / k4);
 }
 
 /* G[s*(n+1)+k], H[...] for k = 0..n, kappa_k = pi k / L  (eq. (Gten_sep)). */
@@ -231,7 +297,7 @@ void or_axis_tables(int n, double L, int terms, const double* a, double* G, doub
 #pragma omp parallel for schedule(dynamic, 16)
     for (int idx = 0; idx < rows; ++idx) {
         int s = idx / (n + 1), k = idx % (n + 1);
-        or_integrals_1d(a[s], L, OR_PI * k / L, &G[idx], &H[idx]);
+        or_integrals_1d(a[s], L, k, &G[idx], &H[idx]);
     }
 }
 
