@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the super-potential GS/FFT free-space Poisson solve on GB300.
+
+Metric: grid points per second (output points n^3 per second) of the solve phase
+(Alg. 2; the one-time precompute of Alg. 1 is excluded, as in the paper's timings) on
+the 256^3 workload: the C-infinity bump density exp(-1/(1 - r^2/0.64)) on [-1,1]^3,
+FP64 (value) with the FP32 path reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 the script runs under torch.distributed.run, one rank per GPU; each rank
+solves its own copy of the workload (independent solves, no collective besides the
+timing barrier and the max-over-ranks reduction), so the scaling is weak.
+
+Timing: W untimed solves, then a barrier and a device synchronise, then exactly K
+solves bracketed by CUDA events on the launching stream, a synchronise, a barrier; the
+step time is the maximum over ranks.  Three rho/u buffer pairs rotate, each larger
+than the 129 MB L2 (with a 537 MB workspace), so no step starts with its input in L2.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+BOX = (-1.0, 1.0)
+ORACLE_SAMPLE_N = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", nargs=3, metavar=("N", "PRECISION", "SOLVES"),
+                    help="only build one plan and run SOLVES solves (a small target for ncu)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (CUDA cores; the tensor path is no faster)
+
+
+def pass_model(n, prec):
+    """Algorithmic bytes and flops per launch of each pass of the five-pass solve.
+
+    Bytes: the pass's compulsory reads and writes (real in/out at 8 or 4 B, complex
+    workspace at 16 or 8 B, the multiplier octant once).  Flops: 5 N log2 N per complex
+    length-N line transform (2.5 N log2 N per real line) plus 2 per multiplier use.
+    """
+    c = 16 if prec == "fp64" else 8
+    r = 8 if prec in ("fp64", "mixed") else 4
+    m = 8 if prec == "fp64" else 4
+    n0 = n1 = n2 = n
+    N = 2 * n
+    lg = math.log2(N)
+    half = n0 * n1 * (n2 + 1)
+    full = n0 * 2 * n1 * (n2 + 1)
+    out = {
+        "z_forward": (r * n0 * n1 * n2 + c * half, n0 * n1 * 2.5 * N * lg),
+        "y_forward": (c * half + c * full, n0 * (n2 + 1) * 5 * N * lg),
+        "x_multiply": (2 * c * full + m * (n0 + 1) * (n1 + 1) * (n2 + 1),
+                       2 * n1 * (n2 + 1) * (10 * N * lg + 2 * N)),
+        "y_inverse": (c * full + c * half, n0 * (n2 + 1) * 5 * N * lg),
+        "z_inverse": (c * half + r * n0 * n1 * n2, n0 * n1 * 2.5 * N * lg),
+    }
+    return out
+
+
+def minimal_bytes_per_point(prec):
+    """Bytes per output point of the minimal three-pass schedule (forward plane pass,
+    x-pencil pass with the multiplier, inverse plane pass)."""
+    return 152.0 if prec == "fp64" else 76.0
+
+
+def source_hash():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2506_04489_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        cur = source_hash()
+        with open(path) as f:
+            for line in f:
+                t = line.split()
+                if len(t) == 4 and not line.startswith("#") and t[0] == kernel and t[1] == workload and t[3] == cur:
+                    return float(t[2])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.05)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                sm.append(float(t[1]))
+                mx.append(float(t[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- dist
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(steps=1, warmup=0):
+    """The FP64 CPU oracle on a bounded sample: 128^3 solves of the same density and box
+    (solve phase only; its own tables built first, untimed), all host threads."""
+    import numpy as np
+
+    import oracle
+    from paper_2506_04489_gb300 import workloads as W
+    oracle.set_threads(os.cpu_count() or 1)
+    n = ORACLE_SAMPLE_N
+    _, _, M = oracle.plan_tables(n, *BOX)
+    rho = W.bump_profile(n, *BOX)
+    for _ in range(warmup):
+        oracle.solve(M, rho)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.solve(M, rho)
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    return {"value": n ** 3 / mean, "unit": "grid pts/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{steps} oracle solves of the bump density at {n}^3 on [-1,1]^3 (1/8 of the {N_GRID}^3 "
+                      f"workload's points; solve phase only, tables built first), mean {mean:.2f} s"}, mean
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cpu, mean = oracle_sample(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": f"grid pts/s at {N_GRID}^3 (FP64 oracle on host cores, bounded sample)",
+            "value": cpu["value"], "unit": "grid pts/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"bump exp(-1/(1-r^2/0.64)) on [-1,1]^3, {ORACLE_SAMPLE_N}^3 sample of the "
+                                   f"{N_GRID}^3 solve, FP64", "grid": ORACLE_SAMPLE_N},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "grid pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def time_solves(plan, rhos, outs, steps, warmup, world, stream):
+    import torch
+    for i in range(warmup):
+        plan.solve(rhos[i % len(rhos)], outs[i % len(outs)], stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    plan.pass_times()  # drop anything recorded before the timed region
+    plan.set_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(steps):
+        plan.solve(rhos[i % len(rhos)], outs[i % len(outs)], stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    plan.set_timing(False)
+    ms = start.elapsed_time(end)
+    return max_over_ranks(ms, world), plan.pass_times()
+
+
+def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
+    model = pass_model(n, prec)
+    name = max(passes, key=lambda k: passes[k][0])
+    tot_ms, launches = passes[name]
+    avg_s = tot_ms / max(launches, 1) / 1e3
+    nbytes, nflops = model[name]
+    workload = f"n{n}_{prec}"
+    if prec == "fp64":
+        achieved = nflops / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); HBM view in hbm_roofline",
+                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
+    else:
+        achieved = nbytes / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "algorithmic_bytes": nbytes}
+    share = {k: round(v[0] / sum(x[0] for x in passes.values()), 4) for k, v in passes.items()}
+    roof["pass_share"] = share
+    return roof
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2506_04489_gb300 import Plan, workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    rho_np = W.bump_profile(n, *BOX)
+    results = {}
+    clocks = None
+    for prec in ("fp64", "fp32"):
+        plan = Plan(n, BOX[0], BOX[1], precision=prec)
+        dt = plan.dtype
+        base = torch.from_numpy(rho_np).to(dev, dtype=dt)
+        rhos = [base.clone() for _ in range(3)]
+        outs = [torch.empty_like(base) for _ in range(3)]
+        sampler = ClockSampler(local) if prec == "fp64" else None
+        ms, passes = time_solves(plan, rhos, outs, args.steps, args.warmup, world, stream)
+        if sampler is not None:
+            clocks = sampler.stop()
+        ms_step = ms / args.steps
+        value = world * n ** 3 / (ms_step / 1e3)
+        roof = roofline_for(prec, n, passes, args.steps, hbm_peak, peak_kind)
+        hbm_frac = minimal_bytes_per_point(prec) * n ** 3 / (ms_step / 1e3) / 1e9 / hbm_peak
+        launches = sum(v[1] for v in passes.values())
+        results[prec] = {"value": value, "ms_per_step": ms_step, "roofline": roof,
+                         "hbm_roofline": {"frac": hbm_frac, "bytes_per_point": minimal_bytes_per_point(prec),
+                                          "peak_gbs": hbm_peak, "note": "bytes of the minimal 3-pass schedule / "
+                                          "solve time / measured HBM bandwidth"},
+                         "gpu_launches": launches}
+        # end to end through the public API: pinned host rho -> device -> solve -> pinned host u
+        if prec == "fp64":
+            host_in = torch.from_numpy(rho_np).to(dtype=dt).pin_memory()
+            host_out = torch.empty(host_in.shape, dtype=dt, pin_memory=True)
+            for _ in range(max(1, args.warmup)):
+                plan.solve(host_in, host_out, stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e2e_steps = max(3, args.steps // 2)
+            s.record(stream)
+            for _ in range(e2e_steps):
+                plan.solve(host_in, host_out, stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            e2e_ms = max_over_ranks(s.elapsed_time(e), world) / e2e_steps
+            results["e2e"] = {"value": world * n ** 3 / (e2e_ms / 1e3), "unit": "grid pts/s",
+                              "ms_per_step": e2e_ms, "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+                              "d2h_bytes_per_step": host_out.numel() * host_out.element_size()}
+        plan.close()
+        del rhos, outs, base
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, _ = oracle_sample(steps=2, warmup=0)
+    r64 = results["fp64"]
+    line = {
+        "metric": f"grid pts/s at {n}^3 (FP64 1e-12 vs FP32 1e-5), % HBM roofline",
+        "value": r64["value"], "unit": "grid pts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"bump exp(-1/(1-r^2/0.64)) density on [-1,1]^3, {n}^3 grid, padded {2 * n}^3, "
+                               f"solve phase (Alg. 2), one independent solve per GPU",
+                   "grid": n, "box": list(BOX), "precision": "fp64",
+                   "l2": "inputs larger than L2: 3 rotating rho/u pairs of "
+                         f"{8 * n ** 3 / 1e6:.0f} MB plus the workspace",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": r64["roofline"],
+        "hbm_roofline": r64["hbm_roofline"],
+        "fp32": {"value": results["fp32"]["value"], "unit": "grid pts/s",
+                 "ms_per_step": results["fp32"]["ms_per_step"], "roofline": results["fp32"]["roofline"],
+                 "hbm_roofline": results["fp32"]["hbm_roofline"]},
+        "e2e": results["e2e"],
+        "gpu_launches": r64["gpu_launches"],
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "kernel_sources": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_case(args):
+    """One plan of grid N^3 and the given precision, then SOLVES solves of the bump
+    density: the launch sequence that the ncu summaries under profiles/ capture."""
+    import torch
+
+    from paper_2506_04489_gb300 import Plan, workloads as W
+    n, prec, k = int(args.profile[0]), args.profile[1], int(args.profile[2])
+    plan = Plan(n, BOX[0], BOX[1], precision=prec)
+    rho = torch.from_numpy(W.bump_profile(n, *BOX)).cuda().to(plan.dtype)
+    out = torch.empty_like(rho)
+    for _ in range(k):
+        plan.solve(rho, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": {"n": n, "precision": prec, "solves": k}}))
+    plan.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.profile:
+        return run_profile_case(args)
+    if args.impl == "reference":
+        # host-only arm: rank 0 times the oracle, the other ranks exit without work
+        return run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+    world, rank, local = dist_init()
+    rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

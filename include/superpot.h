@@ -1,0 +1,171 @@
+/*
+ * superpot.h -- C ABI of the GB300 (sm_103a) super-potential GS/FFT solver for the
+ * free-space Poisson equation  -Laplacian(u) = rho  in R^3  (Exl & Schaffer,
+ * arXiv:2506.04489).
+ *
+ * The solver computes, on a uniform n0 x n1 x n2 grid,
+ *     u = crop( IDFT3( M .* DFT3( pad(rho) ) ) )                       (Alg. 2)
+ * with padding factor 2 per axis (Sec. 2 and Alg. 1) and the real multiplier
+ *     M_k = -|kappa_k|^2 Vhat_k / Ntilde,   Ntilde = 8 n0 n1 n2,      (eq. convtheorem)
+ *     Vhat_k = sum_s w_s (H1 G2 G3 + G1 H2 G3 + G1 G2 H3)              (eq. Gten_sep)
+ * built from the Gaussian-sum (GS) approximation 1/(8 pi r) ~ sum_s w_s exp(-a_s r^2)
+ * on (eps, delta] (eq. sin_1_x) and the one-dimensional integrals
+ *     G_p,s(k) = 2 int_0^{L_p} exp(-a_s y^2) cos(kappa y) dy,
+ *     H_p,s(k) = 2 int_0^{L_p} y^2 exp(-a_s y^2) cos(kappa y) dy,     kappa = pi k / L_p.
+ *
+ * Geometry (the reading of Sec. 3 that reproduces the paper's tables): grid points
+ * x_j = lo + j h, j = 0..n-1, h = (hi - lo)/(n - 1); the padded period is 2 n h and the
+ * kernel window is [-L, L] with L = n h per axis.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are C order [x][y][z] (z fastest), n0 x n1 x n2 elements.
+ *   - Device pointers are CUDA device (or managed) memory of the current device.
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     All work is stream-ordered; no entry point below synchronises the host unless
+ *     it says so.
+ *   - Every call returns sp_status; nothing throws across the ABI.  On failure
+ *     sp_last_error() returns a message for the calling host thread.
+ *   - A plan is not thread-safe: one host thread at a time may use it, and solves
+ *     issued on different streams of one plan share its workspace and therefore must
+ *     not overlap on the GPU.
+ */
+#ifndef SUPERPOT_H
+#define SUPERPOT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SP_FP64 = 0,  /* rho, u float64; FFT passes and multiplier in FP64              */
+    SP_FP32 = 1,  /* rho, u float32; FFT passes in FP32, multiplier rounded to FP32  */
+    SP_MIXED = 2  /* rho, u float64; FFT passes in FP32 (FP32 accumulation)          */
+} sp_precision;
+
+typedef enum {
+    SP_OK = 0,
+    SP_ERR_INVALID = 1,          /* bad argument (null pointer, bad box, ...)          */
+    SP_ERR_UNSUPPORTED_SIZE = 2, /* n < 2, or 2n has a prime factor other than 2 and 3 */
+    SP_ERR_OOM = 3,              /* device allocation failed                            */
+    SP_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed         */
+    SP_ERR_TIMEOUT = 5,          /* a bounded device wait gave up                       */
+    SP_ERR_NOT_READY = 6         /* sp_kernel_precompute has not been run on the plan   */
+} sp_status;
+
+typedef struct sp_plan_s* sp_plan;
+typedef void* sp_stream; /* a cudaStream_t */
+
+/*
+ * sp_plan_create -- validate the problem and allocate the plan's device memory
+ * (Alg. 1 inputs).
+ *   out        : receives the plan handle (set to NULL on failure).
+ *   n[3]       : grid points per axis, each >= 2 with 2n a product of 2s and 3s
+ *                (the padded FFT lengths), 2n <= 4096.
+ *   box_lo/hi  : box faces per axis, hi > lo (the grid spans them inclusively).
+ *   padding    : must be 2 (the paper's padding factor, Alg. 1).
+ *   gs_w, gs_a : host arrays of gs_terms GS weights/exponents (eq. sin_1_x), copied;
+ *                or NULL, NULL, 0 to have sp_kernel_precompute generate them on the
+ *                GPU by sinc quadrature on (eps, delta] with delta the window
+ *                diagonal sqrt(L0^2 + L1^2 + L2^2).
+ *   eps        : GS cutoff (the paper's default is 1e-4); ignored with an explicit table.
+ *   prec       : sp_precision of rho/u and of the solve passes.
+ *   max_batch  : largest batch sp_solve_batched will be given (>= 1); the workspace
+ *                is sized for it.
+ * Device memory: multiplier octant (n0+1)(n1+1)(n2+1) FP64 (+ an FP32 copy for the FP32
+ * passes), twiddles, and a workspace of n0 * 2n1 * (n2+1) complex values per batch
+ * element (see sp_plan_workspace_bytes).  Allocated on the current device.
+ */
+sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
+                         const double box_hi[3], int padding, const double* gs_w,
+                         const double* gs_a, int gs_terms, double eps, sp_precision prec,
+                         int max_batch);
+
+/*
+ * sp_kernel_precompute -- Alg. 1 on the GPU, all in FP64: GS table (if not given),
+ * the 1D integral tables G, H of eq. (Gten_sep) (closed full-line forms where
+ * a_s L^2 >= 40; else composite 16-point Gauss-Legendre with nodes computed on the
+ * device, applied directly for kappa^2 < 4 a_s and, above, to the fourth-derivative
+ * remainder after two exact integrations by parts), the multiplier M_k of
+ * eq. (convtheorem), and the FFT twiddles.
+ * Stream-ordered on `stream`; idempotent.  The plan is ready for solves once the work
+ * on `stream` completes; solves issued on other streams must be ordered after it by
+ * the caller.
+ */
+sp_status sp_kernel_precompute(sp_plan plan, sp_stream stream);
+
+/*
+ * sp_solve -- one solve (Alg. 2): rho (device, n0 x n1 x n2, float64 for SP_FP64 and
+ * SP_MIXED, float32 for SP_FP32) -> u (device, same shape and type).  u may alias rho.
+ * The caller owns rho and u.  Stream-ordered; no host synchronisation.
+ * Returns SP_ERR_NOT_READY before sp_kernel_precompute.
+ */
+sp_status sp_solve(sp_plan plan, const void* rho, void* u, sp_stream stream);
+
+/*
+ * sp_solve_batched -- `batch` independent solves on contiguous arrays
+ * rho[b][x][y][z] -> u[b][x][y][z], 1 <= batch <= max_batch.  Same types and aliasing
+ * rules as sp_solve.
+ */
+sp_status sp_solve_batched(sp_plan plan, const void* rho, void* u, int batch,
+                           sp_stream stream);
+
+/* sp_plan_destroy -- wait for the plan's outstanding work (device synchronise) and free
+ * everything it owns.  NULL is accepted. */
+sp_status sp_plan_destroy(sp_plan plan);
+
+/* Bytes of device workspace the plan holds for solves (0 for a NULL plan). */
+size_t sp_plan_workspace_bytes(const sp_plan plan);
+
+/* Number of GS terms of the plan (known after create for an explicit table, after
+ * precompute for a generated one; 0 before). */
+int sp_plan_gs_terms(const sp_plan plan);
+
+/*
+ * sp_plan_copy_tables -- diagnostic read-back (host synchronising): copies the plan's
+ * FP64 tables to host arrays; any pointer may be NULL to skip it.
+ *   gs_w, gs_a : sp_plan_gs_terms() doubles each.
+ *   M          : (n0+1)(n1+1)(n2+1) doubles, M[k0][k1][k2] = -|kappa|^2 Vhat / Ntilde, the
+ *                multiplier exactly as the solve applies it, |k_p| = 0..n_p.
+ *   G, H       : for axis `axis`, gs_terms x (n_axis+1) doubles each, [s][k].
+ */
+sp_status sp_plan_copy_tables(sp_plan plan, double* gs_w, double* gs_a, double* M,
+                              int axis, double* G, double* H);
+
+/*
+ * sp_forward_spectrum -- diagnostic: only the forward half of Alg. 2.  Writes the
+ * unnormalised padded DFT of rho, spec[kx][ky][kz] for kx < 2n0, ky < 2n1, kz <= n2,
+ * as interleaved complex (float64 pairs for SP_FP64/SP_MIXED inputs computed in the
+ * plan's pass precision; float32 pairs for SP_FP32).  `spec` is device memory of
+ * 2n0 * 2n1 * (n2+1) complex values.  Uses the plan's workspace.
+ */
+sp_status sp_forward_spectrum(sp_plan plan, const void* rho, void* spec, sp_stream stream);
+
+/*
+ * Pass timing (diagnostic).  With timing enabled, every solve records a CUDA event on its
+ * stream before its first pass and after each pass; sp_plan_pass_times then waits for the
+ * last recorded event, adds up the elapsed time of each pass over all solves recorded
+ * since the previous call, and clears the record.
+ *   sp_plan_set_timing : enable != 0 turns recording on, 0 off (off by default).
+ *   sp_plan_pass_times : total_ms[i] (milliseconds) and launches[i] for pass i (both
+ *                        arrays of max_passes entries, either may be NULL); names[i]
+ *                        (may be NULL) receives a static string naming pass i.  Returns
+ *                        the number of passes of one solve (<= max_passes are written),
+ *                        or -1 on error (see sp_last_error).
+ */
+sp_status sp_plan_set_timing(sp_plan plan, int enable);
+int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char** names,
+                       int max_passes);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* sp_last_error(void);
+
+/* Library version string. */
+const char* sp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUPERPOT_H */

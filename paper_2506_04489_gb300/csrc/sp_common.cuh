@@ -1,0 +1,126 @@
+// Common device types for the super-potential solver: complex values, the small
+// DFT butterflies used by every FFT pass, and error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SP_HD __host__ __device__ __forceinline__
+#define SP_D __device__ __forceinline__
+
+template <class R>
+struct __align__(2 * sizeof(R)) cpx {
+    R re, im;
+};
+
+template <class R> SP_HD cpx<R> mk(R a, R b) { cpx<R> c; c.re = a; c.im = b; return c; }
+template <class R> SP_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <class R> SP_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <class R> SP_HD cpx<R> scale(cpx<R> a, R s) { return mk(a.re * s, a.im * s); }
+template <class R> SP_HD cpx<R> conjg(cpx<R> a) { return mk(a.re, -a.im); }
+// a * b
+template <class R> SP_HD cpx<R> cmul(cpx<R> a, cpx<R> b)
+{
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a * conj(b)
+template <class R> SP_HD cpx<R> cmulc(cpx<R> a, cpx<R> b)
+{
+    return mk(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+// a * (s i), s = +1 or -1
+template <int S, class R> SP_HD cpx<R> mul_si(cpx<R> a)
+{
+    return S > 0 ? mk(-a.im, a.re) : mk(a.im, -a.re);
+}
+
+// ---------------------------------------------------------------------------------
+// Small DFTs in registers: X[q] = sum_r u[r] exp(S * 2 pi i r q / R), S = -1 forward,
+// +1 inverse (unnormalised).  Constants are the exact values cos/sin of multiples of
+// 2 pi / R, written as sqrt expressions.
+// ---------------------------------------------------------------------------------
+template <int S, class R> SP_D void dft2(cpx<R>* u)
+{
+    cpx<R> a = u[0], b = u[1];
+    u[0] = a + b;
+    u[1] = a - b;
+}
+
+template <int S, class R> SP_D void dft3(cpx<R>* u)
+{
+    const R c = R(-0.5);
+    const R s = R(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    cpx<R> a = u[0], b = u[1], d = u[2];
+    cpx<R> t = b + d, v = b - d;
+    cpx<R> m = mk(a.re + c * t.re, a.im + c * t.im);
+    cpx<R> w = mul_si<S>(scale(v, s));
+    u[0] = a + t;
+    u[1] = m + w;
+    u[2] = m - w;
+}
+
+template <int S, class R> SP_D void dft4(cpx<R>* u)
+{
+    cpx<R> a = u[0] + u[2], b = u[0] - u[2];
+    cpx<R> c = u[1] + u[3], d = mul_si<S>(u[1] - u[3]);
+    u[0] = a + c;
+    u[2] = a - c;
+    u[1] = b + d;
+    u[3] = b - d;
+}
+
+// 8 = 2 x 4: even/odd split, twiddles exp(S 2 pi i q / 8).
+template <int S, class R> SP_D void dft8(cpx<R>* u)
+{
+    const R h = R(0.70710678118654752440084436210484904);  // 1/sqrt(2)
+    cpx<R> e[4] = {u[0], u[2], u[4], u[6]};
+    cpx<R> o[4] = {u[1], u[3], u[5], u[7]};
+    dft4<S>(e);
+    dft4<S>(o);
+    // o[1] *= (1 + S i)/sqrt2 ; o[2] *= S i ; o[3] *= (-1 + S i)/sqrt2
+    cpx<R> o1 = scale(o[1] + mul_si<S>(o[1]), h);
+    cpx<R> o2 = mul_si<S>(o[2]);
+    cpx<R> o3 = scale(mul_si<S>(o[3]) - o[3], h);
+    u[0] = e[0] + o[0];
+    u[4] = e[0] - o[0];
+    u[1] = e[1] + o1;
+    u[5] = e[1] - o1;
+    u[2] = e[2] + o2;
+    u[6] = e[2] - o2;
+    u[3] = e[3] + o3;
+    u[7] = e[3] - o3;
+}
+
+template <int S, class R> SP_D void dft_small(int radix, cpx<R>* u)
+{
+    switch (radix) {
+        case 2: dft2<S>(u); break;
+        case 3: dft3<S>(u); break;
+        case 4: dft4<S>(u); break;
+        case 8: dft8<S>(u); break;
+        default: break;
+    }
+}
+
+// Maximum number of radix stages of one transform, and the stage plan for a length.
+#define SP_MAX_STAGES 16
+struct RadixPlan {
+    int nst;
+    int r[SP_MAX_STAGES];
+};
+
+// Factor N (a product of 2s and 3s) into stages, largest radices first: 8s, then a 4
+// or 2 for the remaining power of two, then 3s.  Returns false for other lengths.
+static inline bool sp_radix_plan(int N, RadixPlan* p)
+{
+    p->nst = 0;
+    int m = N, twos = 0, threes = 0;
+    while (m % 2 == 0) { m /= 2; ++twos; }
+    while (m % 3 == 0) { m /= 3; ++threes; }
+    if (m != 1 || N < 2) return false;
+    while (twos >= 3) { p->r[p->nst++] = 8; twos -= 3; }
+    if (twos == 2) p->r[p->nst++] = 4;
+    if (twos == 1) p->r[p->nst++] = 2;
+    for (int i = 0; i < threes; ++i) p->r[p->nst++] = 3;
+    return p->nst <= SP_MAX_STAGES;
+}

@@ -1,0 +1,66 @@
+// Internal declarations shared by the library's translation units: the plan object,
+// the launchers of the setup kernels (Alg. 1) and of the solve passes (Alg. 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "../../include/superpot.h"
+#include "sp_common.cuh"
+
+struct sp_plan_s {
+    int n[3];        // grid points per axis
+    int N[3];        // padded FFT lengths 2n
+    double lo[3], hi[3];
+    double h[3];     // grid spacing (hi - lo)/(n - 1)
+    double L[3];     // window half-width n h
+    sp_precision prec;
+    int max_batch;
+    int ldz;         // row stride (in complex elements) of the kz dimension, >= n2 + 1
+    long long plane; // complex elements per x-plane of the workspace: 2 n1 ldz
+    // GS table (eq. sin_1_x)
+    double eps, delta, h_tau, eta;
+    int gs_terms;    // S + 1 (0 until known)
+    bool gs_user;
+    double* d_gs_w;
+    double* d_gs_a;
+    int gs_cap;      // allocated length of d_gs_w / d_gs_a
+    double* h_gs_a;  // host copy of the exponents (decides the full-line rows)
+    // 1D integral tables per axis [s][k], kept for diagnostics; axes with equal
+    // (n, L) share the table of the first such axis
+    double* d_G[3];
+    double* d_H[3];
+    // multiplier octant [|k1|][|k0|][kz] with row stride ldz, scaled by 1/Ntilde
+    double* d_M64;
+    float* d_M32;
+    // twiddles exp(-2 pi i j / N_p), j < N_p, per axis (FP64 and FP32)
+    cpx<double>* d_tw64[3];
+    cpx<float>* d_tw32[3];
+    RadixPlan rp[3];
+    // solve workspace: max_batch x n0 x 2n1 x ldz complex (pass precision)
+    void* d_work;
+    size_t work_bytes;
+    bool ready;
+    int device;
+    // pass timing (diagnostic): events recorded between passes while timing is on
+    bool timing;
+    int npass;                          // passes of one solve
+    const char* pass_name[8];
+    std::vector<cudaEvent_t> ev;        // (npass + 1) events per recorded solve
+};
+
+// Record a timing event on `st` if the plan is timing (no-op otherwise).
+sp_status sp_mark(sp_plan p, cudaStream_t st);
+
+// Thread-local error message helpers (sp_api.cu).
+sp_status sp_fail(sp_status st, const char* fmt, ...);
+sp_status sp_cuda_check(cudaError_t e, const char* what);
+
+// Setup (sp_setup.cu).  All FP64.
+sp_status sp_setup_run(sp_plan p, cudaStream_t st);
+
+// Solve passes (sp_passes.cu).
+sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
+sp_status sp_run_forward(sp_plan p, const void* rho, void* spec, cudaStream_t st);

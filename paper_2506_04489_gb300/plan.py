@@ -1,0 +1,194 @@
+"""Python face of the C ABI: a solver plan bound to torch tensors and streams."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+_PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+
+def precision_dtype(precision: str):
+    import torch
+    return torch.float32 if precision == "fp32" else torch.float64
+
+
+def _vec3(v):
+    if np.isscalar(v):
+        return (v, v, v)
+    v = tuple(v)
+    if len(v) != 3:
+        raise ValueError("expected a scalar or 3 values")
+    return v
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Solver plan: ``Plan(n, lo, hi, precision="fp64")`` then ``solve(rho)``.
+
+    n, lo, hi : grid points and box faces per axis (scalars apply to all axes).
+    precision : "fp64", "fp32" or "mixed" (float64 I/O, FP32 passes).
+    eps       : GS cutoff when the GS table is generated (default 1e-4, Alg. 1).
+    gs        : optional explicit GS table (weights, exponents) as float64 arrays.
+    max_batch : largest batch for ``solve_batched``.
+    precompute: run Alg. 1 on the current stream at construction.
+    """
+
+    def __init__(self, n, lo, hi, precision: str = "fp64", eps: float = 1e-4, gs=None,
+                 max_batch: int = 1, precompute: bool = True, stream=None):
+        from . import _native as N
+        self._N = N
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {list(_PREC)}")
+        self.n = tuple(int(x) for x in _vec3(n))
+        self.lo = tuple(float(x) for x in _vec3(lo))
+        self.hi = tuple(float(x) for x in _vec3(hi))
+        self.precision = precision
+        self.max_batch = int(max_batch)
+        n_c = (ctypes.c_int * 3)(*self.n)
+        lo_c = (ctypes.c_double * 3)(*self.lo)
+        hi_c = (ctypes.c_double * 3)(*self.hi)
+        if gs is not None:
+            w = np.ascontiguousarray(gs[0], dtype=np.float64)
+            a = np.ascontiguousarray(gs[1], dtype=np.float64)
+            wp, ap, terms = w.ctypes.data_as(N._dp), a.ctypes.data_as(N._dp), len(w)
+        else:
+            wp = ap = None
+            terms = 0
+        h = ctypes.c_void_p()
+        N.check(N.lib.sp_plan_create(ctypes.byref(h), n_c, lo_c, hi_c, 2, wp, ap, terms, float(eps),
+                                     _PREC[precision], self.max_batch), "sp_plan_create")
+        self._h = h
+        self.dtype = precision_dtype(precision)
+        if precompute:
+            self.precompute(stream)
+
+    # ----------------------------------------------------------------- lifecycle
+    def precompute(self, stream=None) -> None:
+        self._N.check(self._N.lib.sp_kernel_precompute(self._h, _stream_handle(stream)), "sp_kernel_precompute")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._N.check(self._N.lib.sp_plan_destroy(self._h), "sp_plan_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._N.lib.sp_plan_workspace_bytes(self._h))
+
+    @property
+    def gs_terms(self) -> int:
+        return int(self._N.lib.sp_plan_gs_terms(self._h))
+
+    # ----------------------------------------------------------------- solves
+    def _check_io(self, t, batch: bool):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected a CUDA torch.Tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"expected dtype {self.dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        shape = tuple(t.shape[1:]) if batch else tuple(t.shape)
+        if shape != self.n:
+            raise ValueError(f"expected grid shape {self.n}, got {shape}")
+
+    def solve(self, rho, out=None, stream=None):
+        """u = crop(IDFT3(M .* DFT3(pad(rho)))) (Alg. 2); ``out`` may be ``rho``.
+
+        A CPU ``rho`` (pinned for asynchronous copies) is copied to a device staging
+        buffer, solved there and copied back into ``out`` (a CPU tensor, allocated
+        pinned if not given); the copies are ordered on the same stream.
+        """
+        import torch
+        if isinstance(rho, torch.Tensor) and not rho.is_cuda:
+            return self._solve_host(rho, out, stream)
+        self._check_io(rho, False)
+        if out is None:
+            out = torch.empty_like(rho)
+        self._check_io(out, False)
+        self._N.check(self._N.lib.sp_solve(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "sp_solve")
+        return out
+
+    def _solve_host(self, rho, out, stream):
+        import torch
+        if rho.dtype != self.dtype or tuple(rho.shape) != self.n or not rho.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.dtype} tensor of shape {self.n}")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        buf = getattr(self, "_stage", None)
+        if buf is None:
+            buf = self._stage = torch.empty(self.n, dtype=self.dtype, device="cuda")
+        if out is None:
+            out = torch.empty(self.n, dtype=self.dtype, pin_memory=True)
+        with torch.cuda.stream(st):
+            buf.copy_(rho, non_blocking=True)
+            self.solve(buf, buf, st)
+            out.copy_(buf, non_blocking=True)
+        return out
+
+    # ----------------------------------------------------------------- diagnostics
+    def set_timing(self, enable: bool) -> None:
+        self._N.check(self._N.lib.sp_plan_set_timing(self._h, int(bool(enable))), "sp_plan_set_timing")
+
+    def pass_times(self):
+        """{pass name: (total ms, launches)} over the solves recorded since the last call."""
+        N = self._N
+        tot = (ctypes.c_double * 16)()
+        cnt = (ctypes.c_int * 16)()
+        names = (ctypes.c_char_p * 16)()
+        np_ = N.lib.sp_plan_pass_times(self._h, tot, cnt, names, 16)
+        if np_ < 0:
+            raise N.SuperpotError(1, "sp_plan_pass_times")
+        return {names[i].decode(): (tot[i], cnt[i]) for i in range(np_)}
+
+    def solve_batched(self, rho, out=None, stream=None):
+        import torch
+        self._check_io(rho, True)
+        if out is None:
+            out = torch.empty_like(rho)
+        self._check_io(out, True)
+        self._N.check(self._N.lib.sp_solve_batched(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()), int(rho.shape[0]),
+                                                   _stream_handle(stream)), "sp_solve_batched")
+        return out
+
+    def forward_spectrum(self, rho, stream=None):
+        """Diagnostic: padded forward DFT, [2n0, 2n1, n2+1] complex (pass precision)."""
+        import torch
+        self._check_io(rho, False)
+        cdt = torch.complex128 if self.precision == "fp64" else torch.complex64
+        spec = torch.empty((2 * self.n[0], 2 * self.n[1], self.n[2] + 1), dtype=cdt, device=rho.device)
+        self._N.check(self._N.lib.sp_forward_spectrum(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                                      ctypes.c_void_p(spec.data_ptr()), _stream_handle(stream)),
+                      "sp_forward_spectrum")
+        return spec
+
+    def tables(self, axis: int = 0):
+        """Host copies of the FP64 setup tables (synchronises the device)."""
+        N = self._N
+        S = self.gs_terms
+        w = np.empty(S)
+        a = np.empty(S)
+        M = np.empty(tuple(m + 1 for m in self.n))
+        G = np.empty((S, self.n[axis] + 1))
+        H = np.empty((S, self.n[axis] + 1))
+        d = lambda x: x.ctypes.data_as(N._dp)
+        N.check(N.lib.sp_plan_copy_tables(self._h, d(w), d(a), d(M), int(axis), d(G), d(H)), "sp_plan_copy_tables")
+        return {"gs_w": w, "gs_a": a, "M": M, "G": G, "H": H}
