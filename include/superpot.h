@@ -158,6 +158,31 @@ sp_status sp_plan_set_timing(sp_plan plan, int enable);
 int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char** names,
                        int max_passes);
 
+/*
+ * sp_solve_noalloc -- the solve of sp_solve for callers that cannot allocate device
+ * memory when they solve.  (The paper has no counterpart; this is an interface for
+ * programs whose device memory is fixed in advance.)  cudaMalloc/cudaFree can
+ * synchronise the whole device and stall a latency-bound loop, a host framework may
+ * reserve all device memory for its own pool, and an allocation that fails halfway
+ * through a long run is worse than one refused up front.  Such a caller creates and
+ * precomputes the plan while it may allocate, then calls this entry point, which
+ * allocates nothing: no cudaMalloc, cudaFree, or allocating routine of any library.
+ *   plan    : a plan on the current device, precomputed (else SP_ERR_NOT_READY).
+ *   rho, u  : as for sp_solve (device, n0 x n1 x n2, the plan's I/O type; u may alias rho).
+ * The workspace is a static device array of SP_NOALLOC_MAX_BYTES bytes inside this
+ * library (one per GPU that loads the library, held until the process exits) instead
+ * of the plan's workspace.  A grid whose workspace, (16 bytes for SP_FP64, else 8) x
+ * n0 x 2n1 x round_up(n2 + 1, 8), exceeds it is rejected with SP_ERR_UNSUPPORTED_SIZE
+ * (FP64 cubes up to n = 96 and FP32/mixed cubes up to n = 144 fit).
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Every
+ * call shares the one array and overwrites it, so calls whose work overlaps on the
+ * GPU (other streams, other threads, other plans) race and must be serialised by the
+ * caller.  Stream-ordered; no host synchronisation.
+ */
+#define SP_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
+sp_status sp_solve_noalloc(const sp_plan plan, const void* rho, void* u, sp_stream stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sp_last_error(void);
 

@@ -51,6 +51,8 @@ lib.sp_plan_set_timing.restype = ctypes.c_int
 lib.sp_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_pass_times.restype = ctypes.c_int
 lib.sp_plan_pass_times.argtypes = [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
+lib.sp_solve_noalloc.restype = ctypes.c_int
+lib.sp_solve_noalloc.argtypes = [_vp, _vp, _vp, _vp]
 lib.sp_last_error.restype = ctypes.c_char_p
 lib.sp_last_error.argtypes = []
 lib.sp_version.restype = ctypes.c_char_p

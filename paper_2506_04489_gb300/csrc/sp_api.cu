@@ -13,6 +13,8 @@
 
 static thread_local char g_err[1024] = "";
 
+void sp_clear_error(void) { g_err[0] = 0; }
+
 sp_status sp_fail(sp_status st, const char* fmt, ...)
 {
     va_list ap;
@@ -56,7 +58,10 @@ static void free_plan(sp_plan p)
     cudaFree(p->d_M64);
     cudaFree(p->d_M32);
     cudaFree(p->d_work);
-    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->ev) {
+        for (cudaEvent_t e : *p->ev) cudaEventDestroy(e);
+        delete p->ev;
+    }
     free(p->h_gs_a);
     delete p;
 }
@@ -120,8 +125,9 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     p->gs_cap = user ? gs_terms : kGsCap;
     p->gs_terms = user ? gs_terms : 0;
 
+    p->ev = new (std::nothrow) std::vector<cudaEvent_t>();
     p->h_gs_a = (double*)malloc(sizeof(double) * p->gs_cap);
-    if (!p->h_gs_a) {
+    if (!p->h_gs_a || !p->ev) {
         free_plan(p);
         return sp_fail(SP_ERR_OOM, "host allocation failed");
     }
@@ -260,7 +266,7 @@ sp_status sp_mark(sp_plan p, cudaStream_t st)
     cudaEvent_t e;
     sp_status rc = sp_cuda_check(cudaEventCreate(&e), "create timing event");
     if (rc) return rc;
-    p->ev.push_back(e);
+    p->ev->push_back(e);
     return sp_cuda_check(cudaEventRecord(e, st), "record timing event");
 }
 
@@ -284,13 +290,14 @@ extern "C" int sp_plan_pass_times(sp_plan p, double* total_ms, int* launches, co
         if (launches) launches[i] = 0;
         if (names) names[i] = p->pass_name[i];
     }
-    if (np == 0 || p->ev.empty()) return np;
-    if (p->ev.size() % per != 0) { sp_fail(SP_ERR_INVALID, "incomplete timing record"); return -1; }
-    if (sp_cuda_check(cudaEventSynchronize(p->ev.back()), "wait for timing events")) return -1;
-    for (size_t s0 = 0; s0 < p->ev.size(); s0 += per) {
+    std::vector<cudaEvent_t>& ev = *p->ev;
+    if (np == 0 || ev.empty()) return np;
+    if (ev.size() % per != 0) { sp_fail(SP_ERR_INVALID, "incomplete timing record"); return -1; }
+    if (sp_cuda_check(cudaEventSynchronize(ev.back()), "wait for timing events")) return -1;
+    for (size_t s0 = 0; s0 < ev.size(); s0 += per) {
         for (int i = 0; i < np; ++i) {
             float ms = 0.f;
-            if (sp_cuda_check(cudaEventElapsedTime(&ms, p->ev[s0 + i], p->ev[s0 + i + 1]), "elapsed time"))
+            if (sp_cuda_check(cudaEventElapsedTime(&ms, ev[s0 + i], ev[s0 + i + 1]), "elapsed time"))
                 return -1;
             if (i < max_passes) {
                 if (total_ms) total_ms[i] += ms;
@@ -298,8 +305,8 @@ extern "C" int sp_plan_pass_times(sp_plan p, double* total_ms, int* launches, co
             }
         }
     }
-    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
-    p->ev.clear();
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
     return np;
 }
 

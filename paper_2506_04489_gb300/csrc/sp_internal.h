@@ -48,13 +48,16 @@ struct sp_plan_s {
     bool timing;
     int npass;                          // passes of one solve
     const char* pass_name[8];
-    std::vector<cudaEvent_t> ev;        // (npass + 1) events per recorded solve
+    std::vector<cudaEvent_t>* ev;       // (npass + 1) events per recorded solve
+    // Every member is a plain value or pointer, so a copy of the struct is a plain
+    // byte copy that allocates nothing.
 };
 
 // Record a timing event on `st` if the plan is timing (no-op otherwise).
 sp_status sp_mark(sp_plan p, cudaStream_t st);
 
 // Thread-local error message helpers (sp_api.cu).
+void sp_clear_error(void);
 sp_status sp_fail(sp_status st, const char* fmt, ...);
 sp_status sp_cuda_check(cudaError_t e, const char* what);
 
