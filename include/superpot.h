@@ -41,7 +41,10 @@ extern "C" {
 typedef enum {
     SP_FP64 = 0,  /* rho, u float64; FFT passes and multiplier in FP64              */
     SP_FP32 = 1,  /* rho, u float32; FFT passes in FP32, multiplier rounded to FP32  */
-    SP_MIXED = 2  /* rho, u float64; FFT passes in FP32 (FP32 accumulation)          */
+    SP_MIXED = 2, /* rho, u float64; FFT passes in FP32 (FP32 accumulation)          */
+    SP_DF32 = 3   /* rho, u float64; FFT passes and multiplier in double-float: pairs
+                     of FP32 values hi + lo (about 48 significant bits) on the FP32
+                     pipes; padded lengths 2n in {64, 128, 192, 256, 384, 512, 1024}  */
 } sp_precision;
 
 typedef enum {
@@ -73,9 +76,11 @@ typedef void* sp_stream; /* a cudaStream_t */
  *   prec       : sp_precision of rho/u and of the solve passes.
  *   max_batch  : largest batch sp_solve_batched will be given (>= 1); the workspace
  *                is sized for it.
- * Device memory: multiplier octant (n0+1)(n1+1)(n2+1) FP64 (+ an FP32 copy for the FP32
- * passes), twiddles, and a workspace of n0 * 2n1 * (n2+1) complex values per batch
- * element (see sp_plan_workspace_bytes).  Allocated on the current device.
+ * Device memory: multiplier octant (n0+1)(n1+1)(n2+1) FP64 (+ an FP32 or double-float
+ * copy for those passes), twiddles, and a workspace of n0 * 2n1 * (n2+1) complex values
+ * per batch element (see sp_plan_workspace_bytes).  Allocated on the current device.
+ * SP_DF32 plans need every 2n in {64, 128, 192, 256, 384, 512, 1024}
+ * (else SP_ERR_UNSUPPORTED_SIZE).
  */
 sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
                          const double box_hi[3], int padding, const double* gs_w,
@@ -96,8 +101,9 @@ sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
 sp_status sp_kernel_precompute(sp_plan plan, sp_stream stream);
 
 /*
- * sp_solve -- one solve (Alg. 2): rho (device, n0 x n1 x n2, float64 for SP_FP64 and
- * SP_MIXED, float32 for SP_FP32) -> u (device, same shape and type).  u may alias rho.
+ * sp_solve -- one solve (Alg. 2): rho (device, n0 x n1 x n2, float64 for SP_FP64,
+ * SP_MIXED and SP_DF32, float32 for SP_FP32) -> u (device, same shape and type).
+ * u may alias rho.
  * The caller owns rho and u.  Stream-ordered; no host synchronisation.
  * Returns SP_ERR_NOT_READY before sp_kernel_precompute.
  */
@@ -136,9 +142,10 @@ sp_status sp_plan_copy_tables(sp_plan plan, double* gs_w, double* gs_a, double* 
 /*
  * sp_forward_spectrum -- diagnostic: only the forward half of Alg. 2.  Writes the
  * unnormalised padded DFT of rho, spec[kx][ky][kz] for kx < 2n0, ky < 2n1, kz <= n2,
- * as interleaved complex (float64 pairs for SP_FP64/SP_MIXED inputs computed in the
- * plan's pass precision; float32 pairs for SP_FP32).  `spec` is device memory of
- * 2n0 * 2n1 * (n2+1) complex values.  Uses the plan's workspace.
+ * as interleaved complex values of the pass type: float64 pairs (SP_FP64), float32 pairs
+ * (SP_FP32, SP_MIXED), or double-float pairs (SP_DF32: re.hi, re.lo, im.hi, im.lo as
+ * float32).  `spec` is device memory of 2n0 * 2n1 * (n2+1) complex values.  Uses the
+ * plan's workspace.
  */
 sp_status sp_forward_spectrum(sp_plan plan, const void* rho, void* spec, sp_stream stream);
 
@@ -171,7 +178,8 @@ int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char
  *   rho, u  : as for sp_solve (device, n0 x n1 x n2, the plan's I/O type; u may alias rho).
  * The workspace is a static device array of SP_NOALLOC_MAX_BYTES bytes inside this
  * library (one per GPU that loads the library, held until the process exits) instead
- * of the plan's workspace.  A grid whose workspace, (16 bytes for SP_FP64, else 8) x
+ * of the plan's workspace.  A grid whose workspace, (16 bytes for SP_FP64 and SP_DF32,
+ * else 8) x
  * n0 x 2n1 x round_up(n2 + 1, 8), exceeds it is rejected with SP_ERR_UNSUPPORTED_SIZE
  * (FP64 cubes up to n = 96 and FP32/mixed cubes up to n = 144 fit).
  * The first call on a device looks up the array's device address (once per device,

@@ -54,9 +54,11 @@ static void free_plan(sp_plan p)
         }
         cudaFree(p->d_tw64[ax]);
         cudaFree(p->d_tw32[ax]);
+        cudaFree(p->d_twdf[ax]);
     }
     cudaFree(p->d_M64);
     cudaFree(p->d_M32);
+    cudaFree(p->d_Mdf);
     cudaFree(p->d_work);
     if (p->ev) {
         for (cudaEvent_t e : *p->ev) cudaEventDestroy(e);
@@ -79,7 +81,7 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     *out = nullptr;
     if (!n || !box_lo || !box_hi) return sp_fail(SP_ERR_INVALID, "n, box_lo and box_hi must be non-NULL");
     if (padding != 2) return sp_fail(SP_ERR_INVALID, "padding must be 2 (got %d)", padding);
-    if (prec != SP_FP64 && prec != SP_FP32 && prec != SP_MIXED)
+    if (prec != SP_FP64 && prec != SP_FP32 && prec != SP_MIXED && prec != SP_DF32)
         return sp_fail(SP_ERR_INVALID, "unknown precision %d", (int)prec);
     if (max_batch < 1) return sp_fail(SP_ERR_INVALID, "max_batch must be >= 1 (got %d)", max_batch);
     for (int ax = 0; ax < 3; ++ax) {
@@ -87,6 +89,10 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
             return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
                            "n[%d] = %d: need n >= 2 and 2n a product of 2s and 3s, 2n <= %d", ax, n[ax],
                            kMaxLen);
+        if (prec == SP_DF32 && !sp_v2_supported(2 * n[ax]))
+            return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
+                           "n[%d] = %d: double-float passes need 2n in {64, 128, 192, 256, 384, 512, 1024}", ax,
+                           n[ax]);
         if (!(isfinite(box_lo[ax]) && isfinite(box_hi[ax]) && box_hi[ax] > box_lo[ax]))
             return sp_fail(SP_ERR_INVALID, "box axis %d: need finite lo < hi", ax);
     }
@@ -144,12 +150,14 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     SP_ALLOC(p->d_gs_a, sizeof(double) * p->gs_cap);
     const size_t mcount = (size_t)(n[0] + 1) * (n[1] + 1) * p->ldz;
     SP_ALLOC(p->d_M64, sizeof(double) * mcount);
-    if (prec != SP_FP64) SP_ALLOC(p->d_M32, sizeof(float) * mcount);
+    if (prec == SP_FP32 || prec == SP_MIXED) SP_ALLOC(p->d_M32, sizeof(float) * mcount);
+    if (prec == SP_DF32) SP_ALLOC(p->d_Mdf, sizeof(df32) * mcount);
     for (int ax = 0; ax < 3; ++ax) {
         SP_ALLOC(p->d_tw64[ax], sizeof(cpx<double>) * p->N[ax]);
         SP_ALLOC(p->d_tw32[ax], sizeof(cpx<float>) * p->N[ax]);
+        SP_ALLOC(p->d_twdf[ax], sizeof(cpx<df32>) * p->N[ax]);
     }
-    const size_t csize = prec == SP_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+    const size_t csize = (prec == SP_FP64 || prec == SP_DF32) ? 16 : 8;
     p->work_bytes = csize * (size_t)max_batch * n[0] * (size_t)p->plane;
     SP_ALLOC(p->d_work, p->work_bytes);
 #undef SP_ALLOC

@@ -1,0 +1,221 @@
+// Register-resident mixed-radix FFT engine used by the solve passes.
+//
+// A length-N line is transformed by T = N/E threads that each hold E complex values in
+// registers.  Stage s (radix R_s, span P_s = R_0 ... R_{s-1}) is the Stockham step
+//     for i < N/R, k = i mod P:   u_r = x[i + r N/R] * w^{r k N/(P R)},  u = DFT_R(u),
+//                                 y[(i - k) R + k + q P] = u_q,
+// with thread t owning the butterflies i = t + T m, m < E/R.  Between stages the
+// values go through shared memory once (write, barrier, read).  After the last stage
+// thread t holds y[t + T m + q N/R_last]; the inverse transform runs the radices in
+// reverse order, so its first stage wants exactly those values: a diagonal multiplier
+// between a forward and an inverse transform is applied in registers with no exchange.
+// A forward transform whose upper half of inputs is zero (zero padding) has, in its
+// first radix-R stage, exactly inputs r < R/2 nonzero in every butterfly; an inverse
+// whose upper half of outputs is discarded (crop) needs only outputs q < R/2 of its
+// last stage.  Both are pruned at compile time.
+#pragma once
+
+#include "sp_common.cuh"
+#include "sp_df32.cuh"
+
+// ------------------------------------------------------------------ numeric traits
+template <class R> struct Num;
+template <> struct Num<float> {
+    static SP_HD float c(double d) { return (float)d; }
+};
+template <> struct Num<double> {
+    static SP_HD double c(double d) { return d; }
+};
+template <> struct Num<df32> {
+    static SP_HD df32 c(double d) { return df_from_double(d); }
+};
+
+template <class R> SP_D cpx<R> czero() { return mk(Num<R>::c(0.0), Num<R>::c(0.0)); }
+
+// ------------------------------------------------------------------ plans
+// Forward radices: powers of two first (the first stage is radix 8, so zero padding
+// prunes it uniformly), then 3s.  E is a multiple of every radix.
+template <int N> struct FFTPlan;
+template <> struct FFTPlan<64> { static constexpr int NS = 2, E = 8; static constexpr int R[2] = {8, 8}; };
+template <> struct FFTPlan<128> { static constexpr int NS = 3, E = 8; static constexpr int R[3] = {8, 8, 2}; };
+template <> struct FFTPlan<192> { static constexpr int NS = 3, E = 24; static constexpr int R[3] = {8, 8, 3}; };
+template <> struct FFTPlan<256> { static constexpr int NS = 3, E = 8; static constexpr int R[3] = {8, 8, 4}; };
+template <> struct FFTPlan<384> { static constexpr int NS = 4, E = 24; static constexpr int R[4] = {8, 8, 2, 3}; };
+template <> struct FFTPlan<512> { static constexpr int NS = 3, E = 8; static constexpr int R[3] = {8, 8, 8}; };
+template <> struct FFTPlan<1024> { static constexpr int NS = 4, E = 8; static constexpr int R[4] = {8, 8, 8, 2}; };
+
+// radix of stage s of the forward (INV = false) or inverse (reversed) transform
+template <int N, bool INV> constexpr int radix_at(int s)
+{
+    return INV ? FFTPlan<N>::R[FFTPlan<N>::NS - 1 - s] : FFTPlan<N>::R[s];
+}
+template <int N, bool INV> constexpr int span_at(int s)
+{
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= radix_at<N, INV>(i);
+    return p;
+}
+
+// ------------------------------------------------------------------ butterflies
+// X_q = sum_r u_r exp(S 2 pi i r q / R), in place.
+template <int S, class R> SP_D void bf2(cpx<R>* u)
+{
+    cpx<R> a = u[0], b = u[1];
+    u[0] = a + b;
+    u[1] = a - b;
+}
+
+template <int S, class R> SP_D void bf3(cpx<R>* u)
+{
+    const R c = Num<R>::c(-0.5);
+    const R s = Num<R>::c(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    cpx<R> a = u[0], t = u[1] + u[2], v = u[1] - u[2];
+    cpx<R> m = a + scale(t, c);
+    cpx<R> w = mul_si<S>(scale(v, s));
+    u[0] = a + t;
+    u[1] = m + w;
+    u[2] = m - w;
+}
+
+template <int S, class R> SP_D void bf4(cpx<R>* u)
+{
+    cpx<R> a = u[0] + u[2], b = u[0] - u[2];
+    cpx<R> c = u[1] + u[3], d = mul_si<S>(u[1] - u[3]);
+    u[0] = a + c;
+    u[2] = a - c;
+    u[1] = b + d;
+    u[3] = b - d;
+}
+
+// radix 8 as 2 x 4 (even/odd halves, then twiddles exp(S 2 pi i q / 8))
+template <int S, class R> SP_D void bf8_tail(cpx<R>* u, cpx<R> e0, cpx<R> e1, cpx<R> e2, cpx<R> e3, cpx<R> o0,
+                                             cpx<R> o1, cpx<R> o2, cpx<R> o3)
+{
+    const R h = Num<R>::c(0.70710678118654752440084436210484904);
+    cpx<R> t1 = scale(o1 + mul_si<S>(o1), h);
+    cpx<R> t2 = mul_si<S>(o2);
+    cpx<R> t3 = scale(mul_si<S>(o3) - o3, h);
+    u[0] = e0 + o0;
+    u[4] = e0 - o0;
+    u[1] = e1 + t1;
+    u[5] = e1 - t1;
+    u[2] = e2 + t2;
+    u[6] = e2 - t2;
+    u[3] = e3 + t3;
+    u[7] = e3 - t3;
+}
+
+template <int S, class R> SP_D void bf8(cpx<R>* u)
+{
+    cpx<R> a0 = u[0] + u[4], a1 = u[0] - u[4], a2 = u[2] + u[6], a3 = mul_si<S>(u[2] - u[6]);
+    cpx<R> b0 = u[1] + u[5], b1 = u[1] - u[5], b2 = u[3] + u[7], b3 = mul_si<S>(u[3] - u[7]);
+    bf8_tail<S>(u, a0 + a2, a1 + a3, a0 - a2, a1 - a3, b0 + b2, b1 + b3, b0 - b2, b1 - b3);
+}
+
+// radix 8 with u[4..7] = 0
+template <int S, class R> SP_D void bf8_half(cpx<R>* u)
+{
+    cpx<R> a0 = u[0], a2 = u[2], a3 = mul_si<S>(u[2]);
+    cpx<R> b0 = u[1], b2 = u[3], b3 = mul_si<S>(u[3]);
+    bf8_tail<S>(u, a0 + a2, a0 + a3, a0 - a2, a0 - a3, b0 + b2, b0 + b3, b0 - b2, b0 - b3);
+}
+
+template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
+{
+    if constexpr (RAD == 8) {
+        if constexpr (HALF) bf8_half<S>(u);
+        else bf8<S>(u);
+    } else if constexpr (RAD == 4) {
+        bf4<S>(u);
+    } else if constexpr (RAD == 3) {
+        bf3<S>(u);
+    } else {
+        bf2<S>(u);
+    }
+}
+
+// ------------------------------------------------------------------ stages
+// Thread-local view of one line: t = thread index within the line.
+template <class R, int N, bool INV, int ST> struct Stage {
+    static constexpr int E = FFTPlan<N>::E;
+    static constexpr int T = N / E;
+    static constexpr int RAD = radix_at<N, INV>(ST);
+    static constexpr int P = span_at<N, INV>(ST);
+    static constexpr int NB = E / RAD;
+    static constexpr int STRIDE = N / RAD;
+    static constexpr int TWS = N / (P * RAD);  // twiddle table step
+
+    // inputs of this stage from shared memory: v[m RAD + r] = x[t + T m + r N/RAD]
+    template <class Lay> SP_D static void load(cpx<R> (&v)[E], const cpx<R>* sm, const Lay& lay, int t)
+    {
+#pragma unroll
+        for (int m = 0; m < NB; ++m)
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) v[m * RAD + r] = sm[lay(t + T * m + r * STRIDE)];
+    }
+
+    // twiddles and butterflies (S = -1 forward, +1 inverse); HALF: inputs r >= RAD/2 are zero
+    template <int S, bool HALF> SP_D static void compute(cpx<R> (&v)[E], const cpx<R>* tw, int t)
+    {
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            if constexpr (P > 1) {
+                const int i = t + T * m;
+                const int k = i % P;
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cpx<R> w = tw[r * k * TWS];
+                    v[m * RAD + r] = S < 0 ? cmul(v[m * RAD + r], w) : cmulc(v[m * RAD + r], w);
+                }
+            }
+            butterfly<RAD, S, HALF>(&v[m * RAD]);
+        }
+    }
+
+    // outputs of this stage to shared memory: y[(i - k) RAD + k + q P] = v[m RAD + q]
+    template <class Lay> SP_D static void store(const cpx<R> (&v)[E], cpx<R>* sm, const Lay& lay, int t)
+    {
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+            const int i = t + T * m;
+            const int k = i % P;
+            const int base = (i - k) * RAD + k;
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) sm[lay(base + q * P)] = v[m * RAD + q];
+        }
+    }
+};
+
+// Element index held in register slot j after the last stage of a transform (and the
+// input index of slot j for the first stage of the opposite-direction transform).
+template <int N, bool INV> SP_D int last_element(int t, int j)
+{
+    constexpr int E = FFTPlan<N>::E, T = N / E;
+    constexpr int RL = radix_at<N, INV>(FFTPlan<N>::NS - 1);
+    return t + T * (j / RL) + (j % RL) * (N / RL);
+}
+// Element index of register slot j for the first stage of a transform.
+template <int N, bool INV> SP_D int first_element(int t, int j)
+{
+    constexpr int E = FFTPlan<N>::E, T = N / E;
+    constexpr int R0 = radix_at<N, INV>(0);
+    return t + T * (j / R0) + (j % R0) * (N / R0);
+}
+
+// Run stages [0, NS) of one transform.  On entry v holds the stage-0 inputs (slot
+// j = element first_element(t, j)); on return it holds the last stage's outputs (slot
+// j = element last_element(t, j)).  Exchanges go through `sm` with one barrier after
+// each write and one after each read (all threads of the block must call this).
+template <class R, int N, bool INV, int S, bool HALF0, class Lay, int ST = 0>
+SP_D void run_stages(cpx<R> (&v)[FFTPlan<N>::E], cpx<R>* sm, const Lay& lay, const cpx<R>* tw, int t)
+{
+    using St = Stage<R, N, INV, ST>;
+    St::template compute<S, HALF0 && ST == 0>(v, tw, t);
+    if constexpr (ST + 1 < FFTPlan<N>::NS) {
+        St::store(v, sm, lay, t);
+        __syncthreads();
+        Stage<R, N, INV, ST + 1>::load(v, sm, lay, t);
+        __syncthreads();
+        run_stages<R, N, INV, S, HALF0, Lay, ST + 1>(v, sm, lay, tw, t);
+    }
+}

@@ -9,6 +9,7 @@
 
 #include "../../include/superpot.h"
 #include "sp_common.cuh"
+#include "sp_df32.cuh"
 
 struct sp_plan_s {
     int n[3];        // grid points per axis
@@ -35,9 +36,11 @@ struct sp_plan_s {
     // multiplier octant [|k1|][|k0|][kz] with row stride ldz, scaled by 1/Ntilde
     double* d_M64;
     float* d_M32;
+    df32* d_Mdf;     // double-float copy (SP_DF32 plans)
     // twiddles exp(-2 pi i j / N_p), j < N_p, per axis (FP64 and FP32)
     cpx<double>* d_tw64[3];
     cpx<float>* d_tw32[3];
+    cpx<df32>* d_twdf[3];
     RadixPlan rp[3];
     // solve workspace: max_batch x n0 x 2n1 x ldz complex (pass precision)
     void* d_work;
@@ -63,6 +66,16 @@ sp_status sp_cuda_check(cudaError_t e, const char* what);
 
 // Setup (sp_setup.cu).  All FP64.
 sp_status sp_setup_run(sp_plan p, cudaStream_t st);
+
+// Register-resident solve passes for the compiled lengths (sp_v2_*.cu); they return
+// SP_ERR_UNSUPPORTED_SIZE, with no message, when an axis length has no compiled plan.
+sp_status sp_v2_solve_f32(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st, bool mixed);
+sp_status sp_v2_solve_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
+sp_status sp_v2_solve_df(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
+sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t st, bool mixed);
+sp_status sp_v2_forward_f64(sp_plan p, const void* rho, void* spec, cudaStream_t st);
+sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t st);
+bool sp_v2_supported(int N);
 
 // Solve passes (sp_passes.cu).
 sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);

@@ -56,7 +56,7 @@ extern "C" sp_status sp_solve_noalloc(const sp_plan p, const void* rho, void* u,
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
     if (!rho || !u) return sp_fail(SP_ERR_INVALID, "rho and u must be non-NULL device pointers");
     if (!p->ready) return sp_fail(SP_ERR_NOT_READY, "sp_kernel_precompute has not been run on this plan");
-    const size_t csize = p->prec == SP_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+    const size_t csize = (p->prec == SP_FP64 || p->prec == SP_DF32) ? 16 : 8;
     const size_t need = csize * (size_t)p->n[0] * (size_t)p->plane;
     if (need > kScratchBytes)
         return sp_fail(SP_ERR_UNSUPPORTED_SIZE,

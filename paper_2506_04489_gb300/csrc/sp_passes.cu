@@ -366,22 +366,46 @@ sp_status forward_t(sp_plan p, const void* rho, void* spec, cudaStream_t st)
 
 }  // namespace
 
+bool sp_v2_supported(int N)
+{
+    return N == 64 || N == 128 || N == 192 || N == 256 || N == 384 || N == 512 || N == 1024;
+}
+
 sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
 {
+    // register-resident passes where every axis length has a compiled plan
+    sp_status rc = SP_ERR_UNSUPPORTED_SIZE;
+    switch (p->prec) {
+        case SP_FP64: rc = sp_v2_solve_f64(p, rho, u, batch, st); break;
+        case SP_FP32: rc = sp_v2_solve_f32(p, rho, u, batch, st, false); break;
+        case SP_MIXED: rc = sp_v2_solve_f32(p, rho, u, batch, st, true); break;
+        case SP_DF32: rc = sp_v2_solve_df(p, rho, u, batch, st); break;
+    }
+    if (rc != SP_ERR_UNSUPPORTED_SIZE) return rc;
     switch (p->prec) {
         case SP_FP64: return solve_t<double, double>(p, rho, u, batch, st);
         case SP_FP32: return solve_t<float, float>(p, rho, u, batch, st);
         case SP_MIXED: return solve_t<float, double>(p, rho, u, batch, st);
+        case SP_DF32: break;
     }
-    return sp_fail(SP_ERR_INVALID, "unknown precision");
+    return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no pass plan for this grid and precision");
 }
 
 sp_status sp_run_forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
 {
+    sp_status rc = SP_ERR_UNSUPPORTED_SIZE;
+    switch (p->prec) {
+        case SP_FP64: rc = sp_v2_forward_f64(p, rho, spec, st); break;
+        case SP_FP32: rc = sp_v2_forward_f32(p, rho, spec, st, false); break;
+        case SP_MIXED: rc = sp_v2_forward_f32(p, rho, spec, st, true); break;
+        case SP_DF32: rc = sp_v2_forward_df(p, rho, spec, st); break;
+    }
+    if (rc != SP_ERR_UNSUPPORTED_SIZE) return rc;
     switch (p->prec) {
         case SP_FP64: return forward_t<double, double>(p, rho, spec, st);
         case SP_FP32: return forward_t<float, float>(p, rho, spec, st);
         case SP_MIXED: return forward_t<float, double>(p, rho, spec, st);
+        case SP_DF32: break;
     }
-    return sp_fail(SP_ERR_INVALID, "unknown precision");
+    return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no pass plan for this grid and precision");
 }

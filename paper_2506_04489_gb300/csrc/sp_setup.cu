@@ -274,8 +274,14 @@ __global__ void k_to_f32(long long count, const double* in, float* out)
     if (i < count) out[i] = (float)in[i];
 }
 
+__global__ void k_to_df(long long count, const double* in, df32* out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = df_from_double(in[i]);
+}
+
 // ------------------------------------------------------------------------- K7
-__global__ void k_twiddles(int N, cpx<double>* tw64, cpx<float>* tw32)
+__global__ void k_twiddles(int N, cpx<double>* tw64, cpx<float>* tw32, cpx<df32>* twdf)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -283,6 +289,7 @@ __global__ void k_twiddles(int N, cpx<double>* tw64, cpx<float>* tw32)
     sincospi(2.0 * (double)j / (double)N, &s, &c);
     tw64[j] = mk(c, -s);
     tw32[j] = mk((float)c, (float)-s);
+    twdf[j] = mk(df_from_double(c), df_from_double(-s));
 }
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -406,11 +413,12 @@ sp_status sp_setup_run(sp_plan p, cudaStream_t st)
         }
         long long mcount = rows_total * p->ldz;
         if (p->d_M32) k_to_f32<<<nblk(mcount, 256), 256, 0, st>>>(mcount, p->d_M64, p->d_M32);
+        if (p->d_Mdf) k_to_df<<<nblk(mcount, 256), 256, 0, st>>>(mcount, p->d_M64, p->d_Mdf);
         if ((rc = sp_cuda_check(cudaGetLastError(), "multiplier kernels"))) return rc;
     }
     // K7: twiddles
     for (int ax = 0; ax < 3; ++ax) {
-        k_twiddles<<<nblk(p->N[ax], 256), 256, 0, st>>>(p->N[ax], p->d_tw64[ax], p->d_tw32[ax]);
+        k_twiddles<<<nblk(p->N[ax], 256), 256, 0, st>>>(p->N[ax], p->d_tw64[ax], p->d_tw32[ax], p->d_twdf[ax]);
     }
     return sp_cuda_check(cudaGetLastError(), "twiddle kernel");
 }

@@ -1,0 +1,18 @@
+// v2 solve passes instantiated for double-float arithmetic (FP64 input and output,
+// passes on pairs of FP32 values, see sp_df32.cuh).
+#include "sp_v2.cuh"
+
+namespace v2 {
+template <> const void* Tabs<df32>::tw(sp_plan p, int ax) { return p->d_twdf[ax]; }
+template <> const void* Tabs<df32>::M(sp_plan p) { return p->d_Mdf; }
+}  // namespace v2
+
+sp_status sp_v2_solve_df(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
+{
+    return v2::solve<df32, double>(p, rho, u, batch, st, true);
+}
+
+sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t st)
+{
+    return v2::forward<df32, double>(p, rho, spec, st);
+}

@@ -1,0 +1,18 @@
+// v2 solve passes instantiated for FP32 arithmetic (FP32 and mixed-precision plans).
+#include "sp_v2.cuh"
+
+namespace v2 {
+template <> const void* Tabs<float>::tw(sp_plan p, int ax) { return p->d_tw32[ax]; }
+template <> const void* Tabs<float>::M(sp_plan p) { return p->d_M32; }
+}  // namespace v2
+
+sp_status sp_v2_solve_f32(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st, bool mixed)
+{
+    return mixed ? v2::solve<float, double>(p, rho, u, batch, st, true)
+                 : v2::solve<float, float>(p, rho, u, batch, st, true);
+}
+
+sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t st, bool mixed)
+{
+    return mixed ? v2::forward<float, double>(p, rho, spec, st) : v2::forward<float, float>(p, rho, spec, st);
+}

@@ -1,0 +1,17 @@
+// v2 solve passes instantiated for native FP64 arithmetic.
+#include "sp_v2.cuh"
+
+namespace v2 {
+template <> const void* Tabs<double>::tw(sp_plan p, int ax) { return p->d_tw64[ax]; }
+template <> const void* Tabs<double>::M(sp_plan p) { return p->d_M64; }
+}  // namespace v2
+
+sp_status sp_v2_solve_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
+{
+    return v2::solve<double, double>(p, rho, u, batch, st, true);
+}
+
+sp_status sp_v2_forward_f64(sp_plan p, const void* rho, void* spec, cudaStream_t st)
+{
+    return v2::forward<double, double>(p, rho, spec, st);
+}

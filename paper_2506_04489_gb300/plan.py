@@ -5,7 +5,7 @@ import ctypes
 
 import numpy as np
 
-_PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
+_PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "df32": 3}
 
 
 def precision_dtype(precision: str):
@@ -33,7 +33,8 @@ class Plan:
     """Solver plan: ``Plan(n, lo, hi, precision="fp64")`` then ``solve(rho)``.
 
     n, lo, hi : grid points and box faces per axis (scalars apply to all axes).
-    precision : "fp64", "fp32" or "mixed" (float64 I/O, FP32 passes).
+    precision : "fp64", "fp32", "mixed" (float64 I/O, FP32 passes) or "df32" (float64
+                I/O, double-float passes on the FP32 pipes).
     eps       : GS cutoff when the GS table is generated (default 1e-4, Alg. 1).
     gs        : optional explicit GS table (weights, exponents) as float64 arrays.
     max_batch : largest batch for ``solve_batched``.
@@ -173,8 +174,12 @@ class Plan:
         """Diagnostic: padded forward DFT, [2n0, 2n1, n2+1] complex (pass precision)."""
         import torch
         self._check_io(rho, False)
-        cdt = torch.complex128 if self.precision == "fp64" else torch.complex64
-        spec = torch.empty((2 * self.n[0], 2 * self.n[1], self.n[2] + 1), dtype=cdt, device=rho.device)
+        shape = (2 * self.n[0], 2 * self.n[1], self.n[2] + 1)
+        if self.precision == "df32":  # (re.hi, re.lo, im.hi, im.lo) float32 per value
+            spec = torch.empty(shape + (4,), dtype=torch.float32, device=rho.device)
+        else:
+            cdt = torch.complex128 if self.precision == "fp64" else torch.complex64
+            spec = torch.empty(shape, dtype=cdt, device=rho.device)
         self._N.check(self._N.lib.sp_forward_spectrum(self._h, ctypes.c_void_p(rho.data_ptr()),
                                                       ctypes.c_void_p(spec.data_ptr()), _stream_handle(stream)),
                       "sp_forward_spectrum")

@@ -15,7 +15,12 @@ pytestmark = pytest.mark.gpu
 
 from paper_2506_04489_gb300 import Plan, workloads as W  # noqa: E402
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+TOL = {"fp64": 1e-12, "df32": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+V2_LENGTHS = {64, 128, 192, 256, 384, 512, 1024}
+
+
+def v2_case(n):
+    return all(2 * m in V2_LENGTHS for m in n)
 
 
 def _rel(a, b):
@@ -94,8 +99,10 @@ def mixture_density(n, lo, hi, seed):
 
 
 @pytest.mark.parametrize("n,lo,hi", CASES)
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed", "df32"])
 def test_solve_matches_oracle(oracle, n, lo, hi, precision):
+    if precision == "df32" and not v2_case(n):
+        pytest.skip("double-float passes exist for the compiled padded lengths only")
     rho = mixture_density(n, lo, hi, sum(n))
     _, _, M = oracle_tables(oracle, n, lo, hi)
     ref = oracle.solve(M, rho)
@@ -115,6 +122,9 @@ def test_white_noise_matches_oracle(oracle, n, lo, hi):
     assert _rel(u, ref) <= 1e-12
     u32 = gpu_solve(n, lo, hi, rho, "fp32")
     assert _rel(u32, ref) <= 1e-5
+    if v2_case(n):
+        udf = gpu_solve(n, lo, hi, rho, "df32")
+        assert _rel(udf, ref) <= 1e-12
 
 
 def test_unit_box_gaussian_fp64_and_analytic(oracle):
@@ -140,8 +150,9 @@ def test_128_workload_densities(oracle, dens):
         assert _rel(u, ref) <= TOL[precision], precision
 
 
-def test_forward_spectrum_matches_oracle(oracle):
-    n, lo, hi = (16, 24, 18), (-1, -1, -1), (1, 1, 1)
+@pytest.mark.parametrize("n", [(16, 24, 18), (32, 64, 32), (96, 32, 64)])
+def test_forward_spectrum_matches_oracle(oracle, n):
+    lo, hi = (-1, -1, -1), (1, 1, 1)
     rho = random_density(n, 7)
     plan = Plan(n, lo, hi, precision="fp64")
     spec = plan.forward_spectrum(torch.from_numpy(rho).cuda())
