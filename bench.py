@@ -71,9 +71,9 @@ def pass_model(n, prec):
     workspace at 16 or 8 B, the multiplier octant once).  Flops: 5 N log2 N per complex
     length-N line transform (2.5 N log2 N per real line) plus 2 per multiplier use.
     """
-    c = 16 if prec == "fp64" else 8
-    r = 8 if prec in ("fp64", "mixed") else 4
-    m = 8 if prec == "fp64" else 4
+    c = 16 if prec in ("fp64", "df32") else 8
+    r = 8 if prec in ("fp64", "mixed", "df32") else 4
+    m = 8 if prec in ("fp64", "df32") else 4
     n0 = n1 = n2 = n
     N = 2 * n
     lg = math.log2(N)
@@ -93,7 +93,7 @@ def pass_model(n, prec):
 def minimal_bytes_per_point(prec):
     """Bytes per output point of the minimal three-pass schedule (forward plane pass,
     x-pencil pass with the multiplier, inverse plane pass)."""
-    return 152.0 if prec == "fp64" else 76.0
+    return 152.0 if prec in ("fp64", "df32") else 76.0
 
 
 def source_hash():
@@ -279,6 +279,17 @@ def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
                 "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); HBM view in hbm_roofline",
                 "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
                 "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
+    elif prec == "df32":
+        # FP64-class flops carried out in double-float on the FP32 pipes, counted as FP64
+        # flops of the same algorithm; HBM view of the same kernel beside it
+        achieved = nflops / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "unit": "TFLOP/s (FP64-class)",
+                "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s): the rate native FP64 arithmetic "
+                               "would need; above 1 means the double-float path beats native FP64",
+                "hbm_gbs": nbytes / avg_s / 1e9, "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak,
+                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
     else:
         achieved = nbytes / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -302,13 +313,14 @@ def run_ours(args, world, rank, local):
     rho_np = W.bump_profile(n, *BOX)
     results = {}
     clocks = None
-    for prec in ("fp64", "fp32"):
+    ref_u = None
+    for prec in ("fp64", "df32", "fp32"):
         plan = Plan(n, BOX[0], BOX[1], precision=prec)
         dt = plan.dtype
         base = torch.from_numpy(rho_np).to(dev, dtype=dt)
         rhos = [base.clone() for _ in range(3)]
         outs = [torch.empty_like(base) for _ in range(3)]
-        sampler = ClockSampler(local) if prec == "fp64" else None
+        sampler = ClockSampler(local) if prec == "df32" else None
         ms, passes = time_solves(plan, rhos, outs, args.steps, args.warmup, world, stream)
         if sampler is not None:
             clocks = sampler.stop()
@@ -317,13 +329,22 @@ def run_ours(args, world, rank, local):
         roof = roofline_for(prec, n, passes, args.steps, hbm_peak, peak_kind)
         hbm_frac = minimal_bytes_per_point(prec) * n ** 3 / (ms_step / 1e3) / 1e9 / hbm_peak
         launches = sum(v[1] for v in passes.values())
+        # live accuracy guard: deviation of this path from the native FP64 solve of the
+        # same input (the FP64 path itself is checked against the oracle in tests/)
+        u_dev = outs[(args.steps - 1) % len(outs)].double()
+        if prec == "fp64":
+            ref_u = u_dev.clone()
+            rel_dev = 0.0
+        else:
+            rel_dev = float((u_dev - ref_u).abs().max() / ref_u.abs().max())
         results[prec] = {"value": value, "ms_per_step": ms_step, "roofline": roof,
+                         "max_rel_dev_from_fp64": rel_dev,
                          "hbm_roofline": {"frac": hbm_frac, "bytes_per_point": minimal_bytes_per_point(prec),
                                           "peak_gbs": hbm_peak, "note": "bytes of the minimal 3-pass schedule / "
                                           "solve time / measured HBM bandwidth"},
                          "gpu_launches": launches}
         # end to end through the public API: pinned host rho -> device -> solve -> pinned host u
-        if prec == "fp64":
+        if prec == "df32":
             host_in = torch.from_numpy(rho_np).to(dtype=dt).pin_memory()
             host_out = torch.empty(host_in.shape, dtype=dt, pin_memory=True)
             for _ in range(max(1, args.warmup)):
@@ -350,23 +371,30 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _ = oracle_sample(steps=2, warmup=0)
-    r64 = results["fp64"]
+    r64 = results["df32"]
     line = {
         "metric": f"grid pts/s at {n}^3 (FP64 1e-12 vs FP32 1e-5), % HBM roofline",
         "value": r64["value"], "unit": "grid pts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32x2 (double-float)", "data": "synthetic",
+        "accuracy_path": "double-float passes (hi+lo FP32 pairs) meet the FP64 bar: oracle parity <= 1e-12 "
+                         "in tests/; live max deviation from the native FP64 solve reported below",
         "config": {"workload": f"bump exp(-1/(1-r^2/0.64)) density on [-1,1]^3, {n}^3 grid, padded {2 * n}^3, "
                                f"solve phase (Alg. 2), one independent solve per GPU",
-                   "grid": n, "box": list(BOX), "precision": "fp64",
+                   "grid": n, "box": list(BOX), "precision": "df32 (FP64 in/out)",
                    "l2": "inputs larger than L2: 3 rotating rho/u pairs of "
                          f"{8 * n ** 3 / 1e6:.0f} MB plus the workspace",
                    "parallelism": f"replicas x{world}"},
         "roofline": r64["roofline"],
         "hbm_roofline": r64["hbm_roofline"],
+        "max_rel_dev_from_fp64": r64["max_rel_dev_from_fp64"],
+        "fp64_native": {"value": results["fp64"]["value"], "unit": "grid pts/s",
+                        "ms_per_step": results["fp64"]["ms_per_step"], "roofline": results["fp64"]["roofline"],
+                        "hbm_roofline": results["fp64"]["hbm_roofline"]},
         "fp32": {"value": results["fp32"]["value"], "unit": "grid pts/s",
                  "ms_per_step": results["fp32"]["ms_per_step"], "roofline": results["fp32"]["roofline"],
-                 "hbm_roofline": results["fp32"]["hbm_roofline"]},
+                 "hbm_roofline": results["fp32"]["hbm_roofline"],
+                 "max_rel_dev_from_fp64": results["fp32"]["max_rel_dev_from_fp64"]},
         "e2e": results["e2e"],
         "gpu_launches": r64["gpu_launches"],
         "clocks": clocks,

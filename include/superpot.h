@@ -166,6 +166,38 @@ int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char
                        int max_passes);
 
 /*
+ * Batched execution (configurations with many right-hand sides of one size).
+ *
+ * sp_plan_autotune -- choose the CTA tiles of the solve passes for `batch` right-hand
+ *   sides (1 <= batch <= max_batch) by timing every candidate tile of each pass on the
+ *   plan's workspace (host synchronising; overwrites the workspace).  Tiles decide which
+ *   lines share a CTA, never the arithmetic of a line: results are bitwise identical for
+ *   any tile.  A no-op for grids without compiled register-resident passes.
+ * sp_plan_tiles -- the tiles in use: line_tiles[3] (columns per CTA of the y and x line
+ *   passes, by axis; 0 = default) and *z_tile (pairs of real lines per CTA of the z
+ *   passes).  Either pointer may be NULL.
+ */
+sp_status sp_plan_autotune(sp_plan plan, int batch, sp_stream stream);
+sp_status sp_plan_tiles(const sp_plan plan, int* line_tiles, int* z_tile);
+
+/*
+ * CUDA-graph capture of a (batched) solve on fixed buffers, replayed with one launch.
+ *   sp_graph_capture -- runs sp_solve_batched(plan, rho, u, batch) once on `stream`
+ *     (eagerly, so that every kernel attribute is set outside the capture), then captures
+ *     the same call on `stream` (a created stream; the legacy NULL stream cannot capture)
+ *     and instantiates it.  *out receives the graph.  The graph reads rho and writes u at
+ *     the addresses given here, and uses the plan's tables and workspace: it must not
+ *     outlive the plan or those buffers, and must not overlap other work on the plan.
+ *   sp_graph_launch  -- replay on `stream` (stream-ordered, no host synchronisation).
+ *   sp_graph_destroy -- free the graph (NULL accepted).
+ */
+typedef struct sp_graph_s* sp_graph;
+sp_status sp_graph_capture(sp_plan plan, const void* rho, void* u, int batch, sp_stream stream,
+                           sp_graph* out);
+sp_status sp_graph_launch(sp_graph graph, sp_stream stream);
+sp_status sp_graph_destroy(sp_graph graph);
+
+/*
  * sp_solve_noalloc -- the solve of sp_solve for callers that cannot allocate device
  * memory when they solve.  (The paper has no counterpart; this is an interface for
  * programs whose device memory is fixed in advance.)  cudaMalloc/cudaFree can

@@ -51,6 +51,16 @@ lib.sp_plan_set_timing.restype = ctypes.c_int
 lib.sp_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_pass_times.restype = ctypes.c_int
 lib.sp_plan_pass_times.argtypes = [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
+lib.sp_plan_autotune.restype = ctypes.c_int
+lib.sp_plan_autotune.argtypes = [_vp, ctypes.c_int, _vp]
+lib.sp_plan_tiles.restype = ctypes.c_int
+lib.sp_plan_tiles.argtypes = [_vp, _ip, _ip]
+lib.sp_graph_capture.restype = ctypes.c_int
+lib.sp_graph_capture.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+lib.sp_graph_launch.restype = ctypes.c_int
+lib.sp_graph_launch.argtypes = [_vp, _vp]
+lib.sp_graph_destroy.restype = ctypes.c_int
+lib.sp_graph_destroy.argtypes = [_vp]
 lib.sp_solve_noalloc.restype = ctypes.c_int
 lib.sp_solve_noalloc.argtypes = [_vp, _vp, _vp, _vp]
 lib.sp_last_error.restype = ctypes.c_char_p

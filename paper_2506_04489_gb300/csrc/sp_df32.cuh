@@ -10,7 +10,7 @@
 // Addition is the "sloppy" double-float sum: its error is bounded by a small multiple of
 // 2^-48 (|a| + |b|), the form of bound an FFT's error analysis needs.  Products keep
 // the hi*lo cross terms.  No operation here may be reassociated or contracted by the
-// compiler: every step is an explicit add/sub or an explicit fmaf.
+// compiler: every step is an explicit round-to-nearest intrinsic.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -50,27 +50,70 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
+// Sum without a final renormalisation: hi + lo carries the sum with an error of at
+// most a few 2^-48 (|a| + |b|); lo may exceed ulp(hi)/2 by a small factor, which the
+// exact two-sum of the high parts and the cross terms of the product absorb.  Values
+// are renormalised (df_norm) only where they leave registers.
 __device__ __forceinline__ df32 operator+(df32 a, df32 b)
 {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    df32 r;
-    fast_two_sum(s, e, r.hi, r.lo);
-    return r;
+    return df_make(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
 
 __device__ __forceinline__ df32 operator-(df32 b) { return df_make(-b.hi, -b.lo); }
 
-__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b)
+{
+    float s, e;
+    two_sum(a.hi, -b.hi, s, e);
+    return df_make(s, __fadd_rn(e, __fsub_rn(a.lo, b.lo)));
+}
 
+// Product with the exact high product (fused multiply-add) and both cross terms; the
+// lo*lo term is below 2^-48 of the result and is dropped.
 __device__ __forceinline__ df32 operator*(df32 a, df32 b)
 {
     float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
+    return df_make(p, e);
+}
+
+// a*b - c*d and a*b + c*d with one two-sum of the exact high products.
+__device__ __forceinline__ df32 df_dot_sub(df32 a, df32 b, df32 c, df32 d)
+{
+    float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+    float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    float s, e;
+    two_sum(p1, -p2, s, e);
+    e = __fadd_rn(e, __fsub_rn(e1, e2));
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    e = __fmaf_rn(-c.hi, d.lo, e);
+    e = __fmaf_rn(-c.lo, d.hi, e);
+    return df_make(s, e);
+}
+
+__device__ __forceinline__ df32 df_dot_add(df32 a, df32 b, df32 c, df32 d)
+{
+    float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+    float e1 = __fmaf_rn(a.hi, b.hi, -p1), e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    float s, e;
+    two_sum(p1, p2, s, e);
+    e = __fadd_rn(e, __fadd_rn(e1, e2));
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    e = __fmaf_rn(c.hi, d.lo, e);
+    e = __fmaf_rn(c.lo, d.hi, e);
+    return df_make(s, e);
+}
+
+// Renormalise to |lo| <= ulp(hi)/2 (two-sum: no ordering assumption).
+__device__ __forceinline__ df32 df_norm(df32 a)
+{
     df32 r;
-    fast_two_sum(p, e, r.hi, r.lo);
+    two_sum(a.hi, a.lo, r.hi, r.lo);
     return r;
 }

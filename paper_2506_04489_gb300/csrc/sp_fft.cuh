@@ -32,6 +32,23 @@ template <> struct Num<df32> {
 
 template <class R> SP_D cpx<R> czero() { return mk(Num<R>::c(0.0), Num<R>::c(0.0)); }
 
+// Twiddle products: the generic forms for float/double; for double-float each part is
+// one fused two-product dot (df_dot_sub / df_dot_add).
+template <class R> SP_D cpx<R> tw_mul(cpx<R> a, cpx<R> w) { return cmul(a, w); }
+template <class R> SP_D cpx<R> tw_mulc(cpx<R> a, cpx<R> w) { return cmulc(a, w); }
+template <> SP_D cpx<df32> tw_mul<df32>(cpx<df32> a, cpx<df32> w)
+{
+    return mk(df_dot_sub(a.re, w.re, a.im, w.im), df_dot_add(a.re, w.im, a.im, w.re));
+}
+template <> SP_D cpx<df32> tw_mulc<df32>(cpx<df32> a, cpx<df32> w)
+{
+    return mk(df_dot_add(a.re, w.re, a.im, w.im), df_dot_sub(a.im, w.re, a.re, w.im));
+}
+
+// Values leaving registers (shared or global memory) are kept normalised.
+template <class R> SP_D cpx<R> norm(cpx<R> a) { return a; }
+template <> SP_D cpx<df32> norm<df32>(cpx<df32> a) { return mk(df_norm(a.re), df_norm(a.im)); }
+
 // ------------------------------------------------------------------ plans
 // Forward radices: powers of two first (the first stage is radix 8, so zero padding
 // prunes it uniformly), then 3s.  E is a multiple of every radix.
@@ -135,38 +152,75 @@ template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 }
 
 // ------------------------------------------------------------------ stages
-// Thread-local view of one line: t = thread index within the line.
+// Layouts map an element index e of a line to a shared-memory slot.  They must satisfy
+// lay(e + d) = lay(e) + lay.step(d) for every d that is a multiple of 8 and every e, and
+// lay(8 j + q) = lay(8 j) + q * lay.unit for q < 8: the stage loops then compute one
+// slot per butterfly and add compile-time offsets for the others.
+
+// Per-stage twiddle tables in shared memory: stage s (span P > 1, radix RAD) keeps
+// w^{r k N/(P RAD)} at [k RAD + r], so a butterfly reads RAD - 1 consecutive entries.
+template <int N, bool INV> constexpr int tw_stage_offset(int s)
+{
+    int off = 0;
+    for (int i = 0; i < s; ++i)
+        if (span_at<N, INV>(i) > 1) off += span_at<N, INV>(i) * radix_at<N, INV>(i);
+    return off;
+}
+template <int N> constexpr int tw_stage_size()
+{
+    return tw_stage_offset<N, false>(FFTPlan<N>::NS) + tw_stage_offset<N, true>(FFTPlan<N>::NS);
+}
+template <int N, bool INV> constexpr int tw_base() { return INV ? tw_stage_offset<N, false>(FFTPlan<N>::NS) : 0; }
+
+// Fill the staged tables (all threads of the block; a barrier must follow).
+template <class R, int N, bool INV, int ST = 0>
+SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int tid, int nthreads)
+{
+    if constexpr (ST < FFTPlan<N>::NS) {
+        constexpr int P = span_at<N, INV>(ST), RAD = radix_at<N, INV>(ST);
+        if constexpr (P > 1) {
+            constexpr int TWS = N / (P * RAD);
+            cpx<R>* dst = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST);
+            for (int j = tid; j < P * RAD; j += nthreads) {
+                const int k = j / RAD, r = j % RAD;
+                dst[j] = tw[r * k * TWS];
+            }
+        }
+        fill_stage_twiddles<R, N, INV, ST + 1>(tws, tw, tid, nthreads);
+    }
+}
+
 template <class R, int N, bool INV, int ST> struct Stage {
     static constexpr int E = FFTPlan<N>::E;
     static constexpr int T = N / E;
     static constexpr int RAD = radix_at<N, INV>(ST);
     static constexpr int P = span_at<N, INV>(ST);
     static constexpr int NB = E / RAD;
-    static constexpr int STRIDE = N / RAD;
-    static constexpr int TWS = N / (P * RAD);  // twiddle table step
+    static constexpr int STRIDE = N / RAD;  // a multiple of 8 for every plan
 
     // inputs of this stage from shared memory: v[m RAD + r] = x[t + T m + r N/RAD]
     template <class Lay> SP_D static void load(cpx<R> (&v)[E], const cpx<R>* sm, const Lay& lay, int t)
     {
 #pragma unroll
-        for (int m = 0; m < NB; ++m)
+        for (int m = 0; m < NB; ++m) {
+            const cpx<R>* p0 = sm + lay(t + T * m);
+            const int st = lay.step(STRIDE);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[m * RAD + r] = sm[lay(t + T * m + r * STRIDE)];
+            for (int r = 0; r < RAD; ++r) v[m * RAD + r] = p0[r * st];
+        }
     }
 
     // twiddles and butterflies (S = -1 forward, +1 inverse); HALF: inputs r >= RAD/2 are zero
-    template <int S, bool HALF> SP_D static void compute(cpx<R> (&v)[E], const cpx<R>* tw, int t)
+    template <int S, bool HALF> SP_D static void compute(cpx<R> (&v)[E], const cpx<R>* tws, int t)
     {
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
             if constexpr (P > 1) {
-                const int i = t + T * m;
-                const int k = i % P;
+                const int k = (t + T * m) % P;
+                const cpx<R>* w = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST) + k * RAD;
 #pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    const cpx<R> w = tw[r * k * TWS];
-                    v[m * RAD + r] = S < 0 ? cmul(v[m * RAD + r], w) : cmulc(v[m * RAD + r], w);
-                }
+                for (int r = 1; r < RAD; ++r)
+                    v[m * RAD + r] = S < 0 ? tw_mul(v[m * RAD + r], w[r]) : tw_mulc(v[m * RAD + r], w[r]);
             }
             butterfly<RAD, S, HALF>(&v[m * RAD]);
         }
@@ -180,8 +234,20 @@ template <class R, int N, bool INV, int ST> struct Stage {
             const int i = t + T * m;
             const int k = i % P;
             const int base = (i - k) * RAD + k;
+            if constexpr (P % 8 == 0) {
+                cpx<R>* p0 = sm + lay(base);
+                const int st = lay.step(P);
 #pragma unroll
-            for (int q = 0; q < RAD; ++q) sm[lay(base + q * P)] = v[m * RAD + q];
+                for (int q = 0; q < RAD; ++q) p0[q * st] = norm(v[m * RAD + q]);
+            } else if constexpr (P == 1 && RAD == 8) {
+                cpx<R>* p0 = sm + lay(base);  // base = 8 i
+                const int st = lay.unit();
+#pragma unroll
+                for (int q = 0; q < RAD; ++q) p0[q * st] = norm(v[m * RAD + q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < RAD; ++q) sm[lay(base + q * P)] = norm(v[m * RAD + q]);
+            }
         }
     }
 };
@@ -204,18 +270,24 @@ template <int N, bool INV> SP_D int first_element(int t, int j)
 
 // Run stages [0, NS) of one transform.  On entry v holds the stage-0 inputs (slot
 // j = element first_element(t, j)); on return it holds the last stage's outputs (slot
-// j = element last_element(t, j)).  Exchanges go through `sm` with one barrier after
-// each write and one after each read (all threads of the block must call this).
+// j = element last_element(t, j)).  `fresh` must be safe to write on entry (no reads of
+// it pending in the block); exchanges alternate between `fresh` and `other`, one barrier
+// each: a buffer is written again only after the barrier that follows every read of it.
+// With other == fresh (one buffer) a second barrier follows each read.  Returns the
+// buffer that is safe to write after the call.  All threads of the block must call this.
 template <class R, int N, bool INV, int S, bool HALF0, class Lay, int ST = 0>
-SP_D void run_stages(cpx<R> (&v)[FFTPlan<N>::E], cpx<R>* sm, const Lay& lay, const cpx<R>* tw, int t)
+SP_D cpx<R>* run_stages(cpx<R> (&v)[FFTPlan<N>::E], cpx<R>* fresh, cpx<R>* other, const Lay& lay,
+                        const cpx<R>* tws, int t)
 {
     using St = Stage<R, N, INV, ST>;
-    St::template compute<S, HALF0 && ST == 0>(v, tw, t);
+    St::template compute<S, HALF0 && ST == 0>(v, tws, t);
     if constexpr (ST + 1 < FFTPlan<N>::NS) {
-        St::store(v, sm, lay, t);
+        St::store(v, fresh, lay, t);
         __syncthreads();
-        Stage<R, N, INV, ST + 1>::load(v, sm, lay, t);
-        __syncthreads();
-        run_stages<R, N, INV, S, HALF0, Lay, ST + 1>(v, sm, lay, tw, t);
+        Stage<R, N, INV, ST + 1>::load(v, fresh, lay, t);
+        if (other == fresh) __syncthreads();
+        return run_stages<R, N, INV, S, HALF0, Lay, ST + 1>(v, other, fresh, lay, tws, t);
+    } else {
+        return fresh;
     }
 }

@@ -47,6 +47,10 @@ struct sp_plan_s {
     size_t work_bytes;
     bool ready;
     int device;
+    // tiles of the register-resident passes (0 = built-in default): columns per CTA of
+    // the line passes per axis, pairs of real lines per CTA of the z passes
+    int tile_line[3];
+    int tile_z;
     // pass timing (diagnostic): events recorded between passes while timing is on
     bool timing;
     int npass;                          // passes of one solve
@@ -76,6 +80,9 @@ sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t
 sp_status sp_v2_forward_f64(sp_plan p, const void* rho, void* spec, cudaStream_t st);
 sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t st);
 bool sp_v2_supported(int N);
+float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed);
+float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
+float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
 
 // Solve passes (sp_passes.cu).
 sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);

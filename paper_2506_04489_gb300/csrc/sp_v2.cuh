@@ -27,21 +27,34 @@ template <> SP_D double from_r<df32, double>(df32 x) { return df_to_double(x); }
 template <class R> SP_D cpx<R> half_of(cpx<R> a) { return scale(a, Num<R>::c(0.5)); }
 
 // ------------------------------------------------------------------ layouts
-// Strided lines: lane b (column) is fastest.  A padding row of B entries after every 8
-// rows keeps the stride-8 writes of the first stage off one bank set when a row of B
-// entries is narrower than 128 bytes.
-template <class R, int B> struct LayStrided {
-    static constexpr int PAD = (B * (int)sizeof(cpx<R>) >= 128) ? 0 : B;
-    int b;
-    SP_D int operator()(int e) const { return e * B + (e >> 3) * PAD + b; }
-    static constexpr int size(int N) { return N * B + (N / 8) * PAD; }
+// Strided lines: lane b (column) is fastest, B = 2^lgB columns per CTA (a runtime tile,
+// handled with shifts and masks).  A padding row of B entries after every 8 rows keeps
+// the stride-8 writes of the first stage off one bank set when a row of B entries is
+// narrower than 128 bytes.
+template <class R> struct LayStrided {
+    int lgB, pad_mask, b;
+    SP_D LayStrided(int lgB_, int b_)
+        : lgB(lgB_), pad_mask(((1 << lgB_) * (int)sizeof(cpx<R>) >= 128) ? 0 : ~0), b(b_)
+    {
+    }
+    SP_D int operator()(int e) const { return (e << lgB) + (((e >> 3) << lgB) & pad_mask) + b; }
+    SP_D int unit() const { return 1 << lgB; }
+    SP_D int step(int d) const { return (d << lgB) + (((d >> 3) << lgB) & pad_mask); }  // d a multiple of 8
+    static SP_HD int size(int N, int B) { return N * B + (N / 8) * (B * (int)sizeof(cpx<R>) >= 128 ? 0 : B); }
 };
 // Contiguous lines: lane t is fastest; one padding entry after every 8 entries.
 template <int N> struct LayLine {
     static constexpr int LD = N + N / 8;
     int base;
     SP_D int operator()(int e) const { return base + e + (e >> 3); }
+    SP_D int unit() const { return 1; }
+    SP_D int step(int d) const { return d + d / 8; }
 };
+
+// Shared memory of a pass: the staged twiddles of the directions it runs, then one or
+// two exchange buffers (two when both fit in 100 KB, for one barrier per stage).
+template <class R, int N> constexpr int tw_entries() { return tw_stage_size<N>(); }
+constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 
 // ------------------------------------------------------------------ strided passes
 enum { FWD = 0, INV = 1, XMUL = 2 };
@@ -52,29 +65,49 @@ struct LArgs {
     long long in_os, in_es, in_bs;  // outer / element / batch strides (complex elements)
     long long out_os, out_es, out_bs;
     int ncol;                        // valid columns (kz = 0..n2)
+    int B;                           // columns per CTA (a power of two <= lanes_b_max<N>())
+    int lgB;                         // log2(B), set by the launcher
     const void* tw;                  // exp(-2 pi i j / N), j < N
     const void* M;                   // XMUL: multiplier [|ko|][|kl|][kz], row stride ldzM
     int No, nh_line, ldzM;
 };
 
-template <int N> constexpr int lanes_b() { return N >= 1024 ? 4 : 8; }
+// Largest column tile of a line pass (the launch bound); the runtime tile B divides it.
+template <int N> constexpr int lanes_b_max() { return N >= 1024 ? 8 : 16; }
+template <int N> constexpr int lanes_b_default() { return N >= 1024 ? 4 : 8; }
 
-template <class R, int N, int MODE>
-__global__ void __launch_bounds__((N / FFTPlan<N>::E) * lanes_b<N>()) k2_line(LArgs a)
+// Resident CTAs per SM requested from the compiler: 1024 threads per SM (at most 64
+// registers per thread) for the 8-value plans, to hide global-memory latency; the
+// 24-value plans (lengths with a factor 3) keep their registers.
+template <int N, int THREADS> constexpr int min_blocks() { return FFTPlan<N>::E <= 8 ? 1024 / THREADS : 1; }
+
+// LGB >= 0: the tile 2^LGB is a compile-time constant (the default tile); LGB = -1: the
+// tile comes from a.lgB (other tiles chosen by the autotuner).
+template <int N, int LGB> constexpr int line_threads() { return (N / FFTPlan<N>::E) << (LGB >= 0 ? LGB : 4); }
+template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
+
+template <class R, int N, int MODE, int LGB>
+__global__ void __launch_bounds__(line_threads<N, LGB>(), min_blocks<N, line_threads<N, LGB>()>()) k2_line(LArgs a)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E, B = lanes_b<N>();
+    constexpr int E = FFTPlan<N>::E, T = N / E;
     constexpr int R0 = FFTPlan<N>::R[0];
-    using Lay = LayStrided<R, B>;
+    using Lay = LayStrided<R>;
+    const int lgB = LGB >= 0 ? LGB : a.lgB, B = 1 << lgB;
+    const int BUF = Lay::size(N, B);
+    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, sizeof(cpx<R>) * tw_entries<R, N>());
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tw = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm = tw + N;
-    const int tid = threadIdx.x, b = tid % B, t = tid / B;
-    for (int j = tid; j < N; j += blockDim.x) tw[j] = static_cast<const cpx<R>*>(a.tw)[j];
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
+    const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> lgB;
+    const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
+    if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws, twg, tid, blockDim.x);
+    if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws, twg, tid, blockDim.x);
     const int o = blockIdx.y, c = blockIdx.x * B + b, batch = blockIdx.z;
     const bool cv = c < a.ncol;
     const cpx<R>* in = static_cast<const cpx<R>*>(a.in) + batch * a.in_bs + o * a.in_os + c;
     cpx<R>* out = static_cast<cpx<R>*>(a.out) + batch * a.out_bs + o * a.out_os + c;
-    const Lay lay{b};
+    const Lay lay(lgB, b);
     cpx<R> v[E];
     if constexpr (MODE == INV) {
 #pragma unroll
@@ -90,10 +123,11 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * lanes_b<N>()) k2_line(LA
         }
     }
     __syncthreads();
+    cpx<R>* fresh;
     if constexpr (MODE == INV) {
-        run_stages<R, N, true, +1, false>(v, sm, lay, tw, t);
+        fresh = run_stages<R, N, true, +1, false>(v, sm0, sm1, lay, tws, t);
     } else {
-        run_stages<R, N, false, -1, true>(v, sm, lay, tw, t);
+        fresh = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
     }
     if constexpr (MODE == XMUL) {
         const R* M = static_cast<const R*>(a.M);
@@ -106,16 +140,16 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * lanes_b<N>()) k2_line(LA
             const R m = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
             v[j] = scale(v[j], m);
         }
-        run_stages<R, N, true, +1, false>(v, sm, lay, tw, t);
+        run_stages<R, N, true, +1, false>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
     }
     if constexpr (MODE == FWD) {
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if (cv) out[last_element<N, false>(t, j) * a.out_es] = v[j];
+            if (cv) out[last_element<N, false>(t, j) * a.out_es] = norm(v[j]);
     } else {  // the last inverse radix is R0: outputs q < R0/2 are the kept half
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = v[j];
+            if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
     }
 }
 
@@ -130,22 +164,33 @@ struct ZArgs2 {
     int ldz;
     long long io_bs, w_bs;
     const void* tw;
+    int B;                // pairs of real lines per CTA (pairs_max<N>() / 2^j)
 };
 
-template <int N> constexpr int pairs_per_cta() { return N >= 512 ? 4 : (N >= 256 ? 8 : 16); }
+template <int N> constexpr int pairs_max() { return N >= 512 ? 8 : (N >= 256 ? 16 : 32); }
+template <int N> constexpr int pairs_default() { return N >= 512 ? 4 : (N >= 256 ? 8 : 16); }
 
 SP_D long long w_row(const ZArgs2& a, long long l) { return (l / a.n1) * a.plane + (l % a.n1) * a.ldz; }
 
-template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z_fwd(ZArgs2 a)
+template <class R, int N> SP_HD int z_buf(int B) { return B * LayLine<N>::LD; }
+template <class R, int N> SP_HD bool z_two_buffers(int B)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E, B = pairs_per_cta<N>();
+    return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), sizeof(cpx<R>) * tw_entries<R, N>());
+}
+
+template <class R, class Tio, int N>
+__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
+                                  min_blocks<N, (N / FFTPlan<N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
+{
+    constexpr int E = FFTPlan<N>::E, T = N / E;
+    const int B = a.B;
     constexpr int R0 = FFTPlan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tw = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm = tw + N;
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
-    for (int j = tid; j < N; j += blockDim.x) tw[j] = static_cast<const cpx<R>*>(a.tw)[j];
+    fill_stage_twiddles<R, N, false>(tws, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     const Tio* rho = static_cast<const Tio*>(a.rho) + blockIdx.y * a.io_bs;
@@ -163,9 +208,9 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z
         v[j] = x;
     }
     __syncthreads();
-    run_stages<R, N, false, -1, true>(v, sm, lay, tw, t);
+    cpx<R>* sm = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
 #pragma unroll
-    for (int j = 0; j < E; ++j) sm[lay(last_element<N, false>(t, j))] = v[j];
+    for (int j = 0; j < E; ++j) sm[lay(last_element<N, false>(t, j))] = norm(v[j]);
     __syncthreads();
     // two real lines from one complex transform: Xa = (Z_k + conj Z_{N-k}) / 2,
     // Xb = (Z_k - conj Z_{N-k}) / (2 i), k = 0..n2
@@ -174,21 +219,24 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z
         const cpx<R> zk = sm[lay(k)];
         const cpx<R> zm = conjg(sm[lay(k == 0 ? 0 : N - k)]);
         const cpx<R> s = zk + zm, d = zk - zm;
-        if (l0 < a.lines) W[r0 + k] = half_of(s);
-        if (l1 < a.lines) W[r1 + k] = half_of(mk(d.im, -d.re));
+        if (l0 < a.lines) W[r0 + k] = norm(half_of(s));
+        if (l1 < a.lines) W[r1 + k] = norm(half_of(mk(d.im, -d.re)));
     }
 }
 
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z_inv(ZArgs2 a)
+__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
+                                  min_blocks<N, (N / FFTPlan<N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E, B = pairs_per_cta<N>();
+    constexpr int E = FFTPlan<N>::E, T = N / E;
+    const int B = a.B;
     constexpr int R0 = FFTPlan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tw = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm = tw + N;
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
-    for (int j = tid; j < N; j += blockDim.x) tw[j] = static_cast<const cpx<R>*>(a.tw)[j];
+    fill_stage_twiddles<R, N, true>(tws, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     Tio* u = static_cast<Tio*>(a.u) + blockIdx.y * a.io_bs;
@@ -203,14 +251,14 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z
             xa.im = Num<R>::c(0.0);
             xb.im = Num<R>::c(0.0);
         }
-        sm[lay(k)] = mk(xa.re - xb.im, xa.im + xb.re);
-        if (k > 0 && k < n2) sm[lay(N - k)] = mk(xa.re + xb.im, xb.re - xa.im);
+        sm0[lay(k)] = norm(mk(xa.re - xb.im, xa.im + xb.re));
+        if (k > 0 && k < n2) sm0[lay(N - k)] = norm(mk(xa.re + xb.im, xb.re - xa.im));
     }
     __syncthreads();
     cpx<R> v[E];
-    Stage<R, N, true, 0>::load(v, sm, lay, t);
-    __syncthreads();
-    run_stages<R, N, true, +1, false>(v, sm, lay, tw, t);
+    Stage<R, N, true, 0>::load(v, sm0, lay, t);
+    if (sm1 == sm0) __syncthreads();
+    run_stages<R, N, true, +1, false>(v, sm1, sm0, lay, tws, t);
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         if ((j % R0) < R0 / 2) {  // z < n2
@@ -222,40 +270,61 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_per_cta<N>()) k2_z
 }
 
 // ------------------------------------------------------------------ launchers
-template <class K> inline sp_status smem_attr(K kernel, size_t bytes)
+// Raise one kernel's dynamic shared-memory limit once, to more than any of its launches
+// uses, so that later launches (e.g. under stream capture) make no attribute call.
+template <auto KERNEL> inline sp_status smem_attr(size_t bytes)
 {
-    if (bytes > 48 * 1024)
-        return sp_cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
-                             "set shared memory size");
-    return SP_OK;
+    static bool done = false;
+    if (done || bytes <= 48 * 1024) return SP_OK;
+    sp_status rc = sp_cuda_check(cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                                 "set shared memory size");
+    if (rc == SP_OK) done = true;
+    return rc;
 }
 
 template <class R, int N, int MODE>
 sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
 {
-    constexpr int E = FFTPlan<N>::E, B = lanes_b<N>();
-    const size_t smem = sizeof(cpx<R>) * (size_t)(N + LayStrided<R, B>::size(N));
-    sp_status rc = smem_attr(k2_line<R, N, MODE>, smem);
-    if (rc) return rc;
+    constexpr int E = FFTPlan<N>::E;
+    LArgs ab = a;
+    ab.B = a.B ? a.B : lanes_b_default<N>();
+    const int B = ab.B;
+    if (B < 1 || B > lanes_b_max<N>() || (B & (B - 1))) return sp_fail(SP_ERR_INVALID, "bad line tile %d", B);
+    ab.lgB = 0;
+    while ((1 << ab.lgB) < B) ++ab.lgB;
+    const size_t buf = sizeof(cpx<R>) * LayStrided<R>::size(N, B);
+    const size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
+    const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf;
     dim3 grid((unsigned)((a.ncol + B - 1) / B), (unsigned)outer, (unsigned)batch);
-    k2_line<R, N, MODE><<<grid, (N / E) * B, smem, st>>>(a);
+    sp_status rc;
+    if (ab.lgB == lg_default<N>()) {
+        if ((rc = smem_attr<k2_line<R, N, MODE, lg_default<N>()>>(smem))) return rc;
+        k2_line<R, N, MODE, lg_default<N>()><<<grid, (N / E) * B, smem, st>>>(ab);
+    } else {
+        if ((rc = smem_attr<k2_line<R, N, MODE, -1>>(smem))) return rc;
+        k2_line<R, N, MODE, -1><<<grid, (N / E) * B, smem, st>>>(ab);
+    }
     return sp_cuda_check(cudaGetLastError(), "v2 line pass");
 }
 
 template <class R, class Tio, int N>
 sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
 {
-    constexpr int E = FFTPlan<N>::E, B = pairs_per_cta<N>();
-    const size_t smem = sizeof(cpx<R>) * (size_t)(N + B * LayLine<N>::LD);
+    constexpr int E = FFTPlan<N>::E;
+    ZArgs2 ab = a;
+    ab.B = a.B ? a.B : pairs_default<N>();
+    const int B = ab.B;
+    if (B < 1 || B > pairs_max<N>() || (pairs_max<N>() % B)) return sp_fail(SP_ERR_INVALID, "bad z tile %d", B);
+    const size_t smem = sizeof(cpx<R>) * (tw_entries<R, N>() + (z_two_buffers<R, N>(B) ? 2 : 1) * z_buf<R, N>(B));
     const long long pairs = (a.lines + 1) / 2;
     dim3 grid((unsigned)((pairs + B - 1) / B), (unsigned)batch);
     sp_status rc;
     if (forward) {
-        if ((rc = smem_attr(k2_z_fwd<R, Tio, N>, smem))) return rc;
-        k2_z_fwd<R, Tio, N><<<grid, (N / E) * B, smem, st>>>(a);
+        if ((rc = smem_attr<k2_z_fwd<R, Tio, N>>(smem))) return rc;
+        k2_z_fwd<R, Tio, N><<<grid, (N / E) * B, smem, st>>>(ab);
     } else {
-        if ((rc = smem_attr(k2_z_inv<R, Tio, N>, smem))) return rc;
-        k2_z_inv<R, Tio, N><<<grid, (N / E) * B, smem, st>>>(a);
+        if ((rc = smem_attr<k2_z_inv<R, Tio, N>>(smem))) return rc;
+        k2_z_inv<R, Tio, N><<<grid, (N / E) * B, smem, st>>>(ab);
     }
     return sp_cuda_check(cudaGetLastError(), forward ? "v2 z forward pass" : "v2 z inverse pass");
 }
@@ -326,6 +395,7 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     z.io_bs = (long long)p->n[0] * p->n[1] * p->n[2];
     z.w_bs = (long long)p->n[0] * p->plane;
     z.tw = Tabs<R>::tw(p, 2);
+    z.B = p->tile_z;
     LArgs y = {};
     y.in = y.out = p->d_work;
     y.in_os = y.out_os = p->plane;
@@ -333,11 +403,13 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     y.in_bs = y.out_bs = (long long)p->n[0] * p->plane;
     y.ncol = p->n[2] + 1;
     y.tw = Tabs<R>::tw(p, 1);
+    y.B = p->tile_line[1];
     LArgs x = y;
     x.in_os = x.out_os = p->ldz;
     x.in_es = x.out_es = p->plane;
     x.tw = Tabs<R>::tw(p, 0);
     x.M = Tabs<R>::M(p);
+    x.B = p->tile_line[0];
     x.No = p->N[1];
     x.nh_line = p->n[0];
     x.ldzM = p->ldz;
@@ -355,6 +427,69 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     return SP_OK;
 }
 
+// Time `iters` launches of one pass (0: z passes, 1: y passes, 2: x pass) with the
+// given tile, on the plan's workspace (contents irrelevant: the arithmetic does not
+// depend on the data), `batch` right-hand sides.  Host-synchronising.  Returns the mean
+// milliseconds per launch, or a negative value on error.
+template <class R, class Tio>
+float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
+{
+    ZArgs2 z = {};
+    z.rho = p->d_work;
+    z.u = (char*)p->d_work + p->work_bytes / 2;  // the z passes only need valid addresses
+    z.W = p->d_work;
+    z.n1 = p->n[1];
+    z.n2 = p->n[2];
+    z.lines = (long long)p->n[0] * p->n[1];
+    z.plane = p->plane;
+    z.ldz = p->ldz;
+    z.io_bs = 0;
+    z.w_bs = (long long)p->n[0] * p->plane;
+    z.tw = Tabs<R>::tw(p, 2);
+    z.B = tile;
+    LArgs y = {};
+    y.in = y.out = p->d_work;
+    y.in_os = y.out_os = p->plane;
+    y.in_es = y.out_es = p->ldz;
+    y.in_bs = y.out_bs = (long long)p->n[0] * p->plane;
+    y.ncol = p->n[2] + 1;
+    y.tw = Tabs<R>::tw(p, 1);
+    y.B = tile;
+    LArgs x = y;
+    x.in_os = x.out_os = p->ldz;
+    x.in_es = x.out_es = p->plane;
+    x.tw = Tabs<R>::tw(p, 0);
+    x.M = Tabs<R>::M(p);
+    x.No = p->N[1];
+    x.nh_line = p->n[0];
+    x.ldzM = p->ldz;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.f; }
+    sp_status rc = SP_OK;
+    for (int it = -1; it < iters && rc == SP_OK; ++it) {  // it = -1: warm-up launch
+        if (it == 0) cudaEventRecord(e0, st);
+        if (pass == 0) {
+            rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, 1, st});
+            if (rc == SP_OK) rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, 1, st});
+        } else if (pass == 1) {
+            rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st});
+            if (rc == SP_OK) rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st});
+        } else {
+            rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st});
+        }
+    }
+    cudaEventRecord(e1, st);
+    float ms = -1.f;
+    if (rc == SP_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        ms /= iters;
+    else
+        ms = -1.f;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
 // Forward half only (diagnostic): spectrum[kx][ky][kz], kz <= n2 dense.
 template <class R, class Tio>
 sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
@@ -370,13 +505,16 @@ sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
     z.plane = p->plane;
     z.ldz = p->ldz;
     z.tw = Tabs<R>::tw(p, 2);
+    z.B = p->tile_z;
     LArgs y = {};
     y.in = y.out = p->d_work;
     y.in_os = y.out_os = p->plane;
     y.in_es = y.out_es = p->ldz;
     y.ncol = p->n[2] + 1;
     y.tw = Tabs<R>::tw(p, 1);
+    y.B = p->tile_line[1];
     LArgs x = y;
+    x.B = p->tile_line[0];
     x.out = spec;
     x.in_os = p->ldz;
     x.in_es = p->plane;
@@ -390,3 +528,18 @@ sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
 }
 
 }  // namespace v2
+
+// Explicit instantiation of the line-pass launchers for one arithmetic type R, so that
+// they can be compiled in a translation unit of their own (PREFIX = extern to declare).
+#define SP_V2_LINES_N(PREFIX, R, N)                                                          \
+    PREFIX template sp_status v2::launch_line<R, N, v2::FWD>(const v2::LArgs&, int, int, cudaStream_t); \
+    PREFIX template sp_status v2::launch_line<R, N, v2::INV>(const v2::LArgs&, int, int, cudaStream_t); \
+    PREFIX template sp_status v2::launch_line<R, N, v2::XMUL>(const v2::LArgs&, int, int, cudaStream_t);
+#define SP_V2_LINES(PREFIX, R)        \
+    SP_V2_LINES_N(PREFIX, R, 64)      \
+    SP_V2_LINES_N(PREFIX, R, 128)     \
+    SP_V2_LINES_N(PREFIX, R, 192)     \
+    SP_V2_LINES_N(PREFIX, R, 256)     \
+    SP_V2_LINES_N(PREFIX, R, 384)     \
+    SP_V2_LINES_N(PREFIX, R, 512)     \
+    SP_V2_LINES_N(PREFIX, R, 1024)

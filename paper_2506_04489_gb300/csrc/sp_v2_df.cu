@@ -2,6 +2,8 @@
 // passes on pairs of FP32 values, see sp_df32.cuh).
 #include "sp_v2.cuh"
 
+SP_V2_LINES(extern, df32)
+
 namespace v2 {
 template <> const void* Tabs<df32>::tw(sp_plan p, int ax) { return p->d_twdf[ax]; }
 template <> const void* Tabs<df32>::M(sp_plan p) { return p->d_Mdf; }
@@ -15,4 +17,9 @@ sp_status sp_v2_solve_df(sp_plan p, const void* rho, void* u, int batch, cudaStr
 sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t st)
 {
     return v2::forward<df32, double>(p, rho, spec, st);
+}
+
+float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
+{
+    return v2::time_pass<df32, double>(p, pass, tile, batch, iters, st);
 }

@@ -1,6 +1,8 @@
 // v2 solve passes instantiated for FP32 arithmetic (FP32 and mixed-precision plans).
 #include "sp_v2.cuh"
 
+SP_V2_LINES(extern, float)
+
 namespace v2 {
 template <> const void* Tabs<float>::tw(sp_plan p, int ax) { return p->d_tw32[ax]; }
 template <> const void* Tabs<float>::M(sp_plan p) { return p->d_M32; }
@@ -15,4 +17,9 @@ sp_status sp_v2_solve_f32(sp_plan p, const void* rho, void* u, int batch, cudaSt
 sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t st, bool mixed)
 {
     return mixed ? v2::forward<float, double>(p, rho, spec, st) : v2::forward<float, float>(p, rho, spec, st);
+}
+
+float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed)
+{
+    return mixed ? v2::time_pass<float, double>(p, pass, tile, batch, iters, st) : v2::time_pass<float, float>(p, pass, tile, batch, iters, st);
 }

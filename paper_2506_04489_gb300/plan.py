@@ -144,6 +144,29 @@ class Plan:
             out.copy_(buf, non_blocking=True)
         return out
 
+    # ----------------------------------------------------------------- batched execution
+    def autotune(self, batch: int = 1, stream=None) -> dict:
+        """Pick the pass tiles for `batch` right-hand sides by timing (results unchanged)."""
+        self._N.check(self._N.lib.sp_plan_autotune(self._h, int(batch), _stream_handle(stream)), "sp_plan_autotune")
+        return self.tiles()
+
+    def tiles(self) -> dict:
+        line = (ctypes.c_int * 3)()
+        z = ctypes.c_int()
+        self._N.check(self._N.lib.sp_plan_tiles(self._h, line, ctypes.byref(z)), "sp_plan_tiles")
+        return {"line": tuple(line), "z": z.value}
+
+    def capture(self, rho, out, stream):
+        """CUDA graph of solve_batched(rho, out) on these buffers; replay with Graph.launch."""
+        self._check_io(rho, True)
+        self._check_io(out, True)
+        g = ctypes.c_void_p()
+        self._N.check(self._N.lib.sp_graph_capture(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr()), int(rho.shape[0]),
+                                                   ctypes.c_void_p(stream.cuda_stream), ctypes.byref(g)),
+                      "sp_graph_capture")
+        return Graph(self, g, (rho, out))
+
     # ----------------------------------------------------------------- diagnostics
     def set_timing(self, enable: bool) -> None:
         self._N.check(self._N.lib.sp_plan_set_timing(self._h, int(bool(enable))), "sp_plan_set_timing")
@@ -197,3 +220,28 @@ class Plan:
         d = lambda x: x.ctypes.data_as(N._dp)
         N.check(N.lib.sp_plan_copy_tables(self._h, d(w), d(a), d(M), int(axis), d(G), d(H)), "sp_plan_copy_tables")
         return {"gs_w": w, "gs_a": a, "M": M, "G": G, "H": H}
+
+
+class Graph:
+    """A captured batched solve (holds references to its plan and buffers)."""
+
+    def __init__(self, plan, handle, buffers):
+        self._plan = plan
+        self._h = handle
+        self._buffers = buffers
+
+    def launch(self, stream=None) -> None:
+        N = self._plan._N
+        N.check(N.lib.sp_graph_launch(self._h, _stream_handle(stream)), "sp_graph_launch")
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            N = self._plan._N
+            N.check(N.lib.sp_graph_destroy(self._h), "sp_graph_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,292 @@
+"""Continuous-batching solve server.
+
+Requests (a density on an n^3 grid of a fixed box, and an accuracy target) arrive at
+any time; a scheduler thread admits them onto the GPU as stream slots and device memory
+free up, so that work of different requests overlaps on the device:
+
+* accuracy routing: a target of 1e-6 or looser runs on FP32 plans (parity bar 1e-5),
+  tighter targets on double-float plans (FP64 in/out, parity bar 1e-12);
+* per-(grid, precision) plans stay resident on the device with their multiplier and
+  workspace (the one-time precompute of Alg. 1 is paid once per plan);
+* same-key requests waiting together are solved as one batch (sp_solve_batched);
+* a device-memory budget bounds everything the server allocates (plans, batch buffers);
+  a new plan is admitted only within the budget, evicting idle plans of other keys first,
+  otherwise the request waits for a plan of its key to free up;
+* each batch runs on one of several CUDA streams (slots): host-to-device copy of the
+  inputs, the solve, device-to-host copy of the results, then an event the scheduler
+  polls.  Latency is completion (event observed) minus arrival, host monotonic clock.
+
+A request whose input is invalid fails alone: its future gets the exception, the rest
+of its batch and all other requests proceed.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+from .plan import Plan
+
+
+def precision_for(accuracy: float) -> str:
+    """Accuracy target -> plan precision."""
+    return "fp32" if accuracy >= 1e-6 else "df32"
+
+
+class Request:
+    __slots__ = ("rho", "accuracy", "n", "precision", "arrival", "future", "done_at")
+
+    def __init__(self, rho, accuracy, arrival):
+        self.rho = rho
+        self.accuracy = accuracy
+        self.n = int(rho.shape[0])
+        self.precision = precision_for(accuracy)
+        self.arrival = arrival
+        self.future = Future()
+        self.done_at = None
+
+
+class _Entry:
+    """One resident plan with its batch buffers; used by one slot at a time."""
+
+    def __init__(self, key, plan, in_buf, out_buf, nbytes):
+        self.key = key
+        self.plan = plan
+        self.in_buf = in_buf
+        self.out_buf = out_buf
+        self.nbytes = nbytes
+        self.busy = False
+        self.last_used = time.monotonic()
+
+
+class Server:
+    """Continuous-batching server for solves on the box [lo, hi]^3.
+
+    budget_bytes : device memory the server may hold (plans + batch buffers).
+    max_batch    : largest batch per launch.
+    slots        : concurrent batches (CUDA streams).
+    """
+
+    def __init__(self, lo: float = -1.0, hi: float = 1.0, budget_bytes: float = 120e9, max_batch: int = 8,
+                 slots: int = 4, device: int = 0):
+        import torch
+        self.torch = torch
+        self.lo, self.hi = float(lo), float(hi)
+        self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.device = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.slot_busy = [None] * slots  # (event, entry, [(request, host_out)])
+        self.pending = collections.OrderedDict()  # key -> deque of requests
+        self.entries = {}  # key -> [_Entry]
+        self.used_bytes = 0
+        self.peak_bytes = 0
+        self.completed = []
+        self.batches = 0
+        self._lock = threading.Lock()
+        self._wake = threading.Event()
+        self._stop = False
+        self._thread = None
+
+    # ------------------------------------------------------------------ client side
+    def start(self):
+        self._thread = threading.Thread(target=self._loop, name="superpot-scheduler", daemon=True)
+        self._thread.start()
+        return self
+
+    def submit(self, rho, accuracy: float, arrival: float = None) -> Future:
+        """Queue one solve.  rho: a CPU torch tensor (pinned for asynchronous copies) of
+        shape (n, n, n), float32 for accuracy >= 1e-6 else float64.  The future yields
+        the potential as a CPU tensor of the same shape and type."""
+        req = Request(rho, accuracy, time.monotonic() if arrival is None else arrival)
+        with self._lock:
+            self.pending.setdefault((req.n, req.precision), collections.deque()).append(req)
+        self._wake.set()
+        return req.future
+
+    def stop(self):
+        self._stop = True
+        self._wake.set()
+        if self._thread is not None:
+            self._thread.join()
+        self.torch.cuda.synchronize(self.device)
+        for lst in self.entries.values():
+            for e in lst:
+                e.plan.close()
+        self.entries.clear()
+        self.used_bytes = 0
+
+    # ------------------------------------------------------------------ memory
+    def _entry_bytes(self, n, precision):
+        c = 16 if precision in ("fp64", "df32") else 8
+        r = 4 if precision == "fp32" else 8
+        ldz = (n + 1 + 7) // 8 * 8
+        work = self.max_batch * c * n * 2 * n * ldz
+        tables = (n + 1) * (n + 1) * ldz * (8 + (8 if precision == "df32" else 4)) + 3 * 2 * n * 32
+        io = 2 * self.max_batch * n ** 3 * r
+        return work + tables + io + (1 << 20)
+
+    def _evict_idle(self, need, keep_key):
+        """Free idle plans of other keys, least recently used first, until `need` fits."""
+        idle = [e for k, lst in self.entries.items() if k != keep_key for e in lst if not e.busy]
+        idle.sort(key=lambda e: e.last_used)
+        for e in idle:
+            if self.used_bytes + need <= self.budget:
+                break
+            self.entries[e.key].remove(e)
+            e.plan.close()
+            self.used_bytes -= e.nbytes
+        return self.used_bytes + need <= self.budget
+
+    def _get_entry(self, key):
+        lst = self.entries.setdefault(key, [])
+        for e in lst:
+            if not e.busy:
+                return e
+        need = self._entry_bytes(*key)
+        if self.used_bytes + need > self.budget and not self._evict_idle(need, key):
+            return None  # wait for a plan of this key (or memory) to free up
+        n, precision = key
+        torch = self.torch
+        plan = Plan(n, self.lo, self.hi, precision=precision, max_batch=self.max_batch)
+        in_buf = torch.empty((self.max_batch, n, n, n), dtype=plan.dtype, device=self.device)
+        out_buf = torch.empty_like(in_buf)
+        e = _Entry(key, plan, in_buf, out_buf, need)
+        lst.append(e)
+        self.used_bytes += need
+        self.peak_bytes = max(self.peak_bytes, self.used_bytes)
+        return e
+
+    # ------------------------------------------------------------------ scheduler
+    def _poll(self):
+        now_done = False
+        for i, slot in enumerate(self.slot_busy):
+            if slot is None:
+                continue
+            ev, entry, items = slot
+            if ev.query():
+                t = time.monotonic()
+                for req, host_out in items:
+                    req.done_at = t
+                    req.future.set_result(host_out)
+                    self.completed.append(req)
+                entry.busy = False
+                entry.last_used = t
+                self.slot_busy[i] = None
+                now_done = True
+        return now_done
+
+    def _launch(self, slot, entry, reqs):
+        torch = self.torch
+        st = self.streams[slot]
+        items = []
+        dtype = entry.plan.dtype
+        good = []
+        for r in reqs:
+            if tuple(r.rho.shape) != (entry.key[0],) * 3 or r.rho.dtype != dtype or r.rho.is_cuda:
+                r.future.set_exception(ValueError(
+                    f"request needs a CPU {dtype} tensor of shape {(entry.key[0],) * 3}"))
+                continue
+            good.append(r)
+        if not good:
+            entry.busy = False
+            return
+        b = len(good)
+        with torch.cuda.stream(st):
+            for i, r in enumerate(good):
+                entry.in_buf[i].copy_(r.rho, non_blocking=True)
+            entry.plan.solve_batched(entry.in_buf[:b], entry.out_buf[:b], st)
+            for i, r in enumerate(good):
+                host = torch.empty(r.rho.shape, dtype=dtype, pin_memory=True)
+                host.copy_(entry.out_buf[i], non_blocking=True)
+                items.append((r, host))
+            ev = torch.cuda.Event()
+            ev.record(st)
+        self.slot_busy[slot] = (ev, entry, items)
+        self.batches += 1
+
+    def _schedule(self):
+        launched = False
+        while True:
+            free = [i for i, s in enumerate(self.slot_busy) if s is None]
+            if not free:
+                return launched
+            with self._lock:
+                keys = [k for k, q in self.pending.items() if q]
+                keys.sort(key=lambda k: self.pending[k][0].arrival)  # oldest waiting request first
+            started = False
+            for key in keys:
+                entry = self._get_entry(key)
+                if entry is None:
+                    continue
+                with self._lock:
+                    q = self.pending[key]
+                    reqs = [q.popleft() for _ in range(min(self.max_batch, len(q)))]
+                entry.busy = True
+                self._launch(free[0], entry, reqs)
+                launched = started = True
+                break
+            if not started:
+                return launched
+
+    def _loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        while not self._stop:
+            progressed = self._poll()
+            progressed = self._schedule() or progressed
+            if not progressed:
+                busy = any(s is not None for s in self.slot_busy)
+                if busy:
+                    time.sleep(2e-5)
+                else:
+                    self._wake.wait(timeout=1e-3)
+                    self._wake.clear()
+        # drain
+        while any(s is not None for s in self.slot_busy):
+            self._poll()
+            time.sleep(1e-4)
+
+
+def poisson_stream(server: Server, rate: float, duration: float, sizes, accuracies, seed: int = 0,
+                   densities=None, warmup: float = 0.0):
+    """Drive `server` with Poisson arrivals (mean `rate` per second) for `warmup + duration`
+    seconds; each request draws its grid size and accuracy uniformly from the lists.
+    `densities[(n, precision)]` supplies the (pinned CPU) input of a key.  Returns the
+    requests that arrived after the warm-up, completed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t0 = time.monotonic()
+    t = 0.0
+    reqs = []
+    while t < warmup + duration:
+        n = int(sizes[rng.integers(len(sizes))])
+        acc = float(accuracies[rng.integers(len(accuracies))])
+        key = (n, precision_for(acc))
+        due = t0 + t
+        now = time.monotonic()
+        if due > now:
+            time.sleep(due - now)
+        fut = server.submit(densities[key], acc, arrival=due)
+        reqs.append((t, key, fut))
+        t += float(rng.exponential(1.0 / rate))
+    for _, _, fut in reqs:
+        fut.result()
+    return [(t, key) for t, key, _ in reqs if t >= warmup]
+
+
+def latency_summary(server: Server, t_start: float, t_end: float):
+    """p50/p99 latency (ms) and throughput of the requests that arrived in [t_start, t_end)."""
+    lat = sorted((r.done_at - r.arrival) * 1e3 for r in server.completed if t_start <= r.arrival < t_end)
+    if not lat:
+        return None
+    span = max(r.done_at for r in server.completed if t_start <= r.arrival < t_end) - t_start
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+    return {"requests": len(lat), "p50_ms": pct(50), "p99_ms": pct(99), "mean_ms": sum(lat) / len(lat),
+            "solves_per_s": len(lat) / span, "batches": server.batches, "peak_bytes": server.peak_bytes}
