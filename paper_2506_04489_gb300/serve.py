@@ -37,6 +37,22 @@ def precision_for(accuracy: float) -> str:
     return "fp32" if accuracy >= 1e-6 else "df32"
 
 
+def entry_bytes(n: int, precision: str, max_batch: int) -> int:
+    """Device bytes of one resident plan of an n^3 grid with batch buffers for max_batch
+    requests: workspace, multiplier octant and its pass-precision copy, twiddles, and the
+    input and output batch buffers (plus 1 MiB for small tables)."""
+    c = 16 if precision in ("fp64", "df32") else 8
+    r = 4 if precision == "fp32" else 8
+    ldz = (n + 1 + 7) // 8 * 8
+    work = max_batch * c * n * 2 * n * ldz
+    tables = (n + 1) * (n + 1) * ldz * (8 + (8 if precision == "df32" else 4)) + 3 * 2 * n * 32
+    io = 2 * max_batch * n ** 3 * r
+    return work + tables + io + (1 << 20)
+
+
+Done = collections.namedtuple("Done", "arrival done_at key")
+
+
 class Request:
     __slots__ = ("rho", "accuracy", "n", "precision", "arrival", "future", "done_at")
 
@@ -66,15 +82,18 @@ class _Entry:
 class Server:
     """Continuous-batching server for solves on the box [lo, hi]^3.
 
-    budget_bytes : device memory the server may hold (plans + batch buffers).
-    max_batch    : largest batch per launch.
-    slots        : concurrent batches (CUDA streams).
+    budget_bytes  : device memory the server may hold (plans + batch buffers).
+    max_batch     : largest batch per launch.
+    slots         : concurrent batches (CUDA streams).
+    plans_per_key : resident plans per (n, precision); further requests of a busy key wait
+                    and are batched together when a plan frees up.
     """
 
     def __init__(self, lo: float = -1.0, hi: float = 1.0, budget_bytes: float = 120e9, max_batch: int = 8,
-                 slots: int = 4, device: int = 0):
+                 slots: int = 4, device: int = 0, plans_per_key: int = 2):
         import torch
         self.torch = torch
+        self.plans_per_key = int(plans_per_key)
         self.lo, self.hi = float(lo), float(hi)
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
@@ -122,13 +141,7 @@ class Server:
 
     # ------------------------------------------------------------------ memory
     def _entry_bytes(self, n, precision):
-        c = 16 if precision in ("fp64", "df32") else 8
-        r = 4 if precision == "fp32" else 8
-        ldz = (n + 1 + 7) // 8 * 8
-        work = self.max_batch * c * n * 2 * n * ldz
-        tables = (n + 1) * (n + 1) * ldz * (8 + (8 if precision == "df32" else 4)) + 3 * 2 * n * 32
-        io = 2 * self.max_batch * n ** 3 * r
-        return work + tables + io + (1 << 20)
+        return entry_bytes(n, precision, self.max_batch)
 
     def _evict_idle(self, need, keep_key):
         """Free idle plans of other keys, least recently used first, until `need` fits."""
@@ -142,11 +155,28 @@ class Server:
             self.used_bytes -= e.nbytes
         return self.used_bytes + need <= self.budget
 
+    def prepare(self, keys):
+        """Build the resident plans of each (n, precision) key now, before traffic:
+        plans_per_key of them while the budget allows (the rest are built on demand), so
+        that no allocation or precompute stalls the device once requests flow."""
+        for _ in range(self.plans_per_key):
+            for key in keys:
+                key = (int(key[0]), key[1])
+                lst = self.entries.get(key, [])
+                if len(lst) < self.plans_per_key and self.used_bytes + self._entry_bytes(*key) <= self.budget:
+                    for e in lst:
+                        e.busy = True  # force a new plan rather than reuse
+                    self._get_entry(key)
+                    for e in lst:
+                        e.busy = False
+
     def _get_entry(self, key):
         lst = self.entries.setdefault(key, [])
         for e in lst:
             if not e.busy:
                 return e
+        if len(lst) >= self.plans_per_key:
+            return None  # wait for a plan of this key: its requests batch up meanwhile
         need = self._entry_bytes(*key)
         if self.used_bytes + need > self.budget and not self._evict_idle(need, key):
             return None  # wait for a plan of this key (or memory) to free up
@@ -155,6 +185,9 @@ class Server:
         plan = Plan(n, self.lo, self.hi, precision=precision, max_batch=self.max_batch)
         in_buf = torch.empty((self.max_batch, n, n, n), dtype=plan.dtype, device=self.device)
         out_buf = torch.empty_like(in_buf)
+        # the precompute ran on this thread's current stream; the slot streams are not
+        # ordered after it, so the plan is published only once it has finished
+        torch.cuda.synchronize(self.device)
         e = _Entry(key, plan, in_buf, out_buf, need)
         lst.append(e)
         self.used_bytes += need
@@ -172,8 +205,10 @@ class Server:
                 t = time.monotonic()
                 for req, host_out in items:
                     req.done_at = t
+                    # only (arrival, completion, key) is kept: results belong to the client,
+                    # so their pinned buffers return to the allocator's cache once dropped
+                    self.completed.append(Done(req.arrival, t, (req.n, req.precision)))
                     req.future.set_result(host_out)
-                    self.completed.append(req)
                 entry.busy = False
                 entry.last_used = t
                 self.slot_busy[i] = None
@@ -220,6 +255,13 @@ class Server:
                 keys.sort(key=lambda k: self.pending[k][0].arrival)  # oldest waiting request first
             started = False
             for key in keys:
+                if self._entry_bytes(*key) > self.budget:  # can never be admitted
+                    with self._lock:
+                        q = self.pending[key]
+                        while q:
+                            q.popleft().future.set_exception(MemoryError(
+                                f"a {key[0]}^3 {key[1]} plan needs more than the {self.budget} B budget"))
+                    continue
                 entry = self._get_entry(key)
                 if entry is None:
                     continue
@@ -261,7 +303,16 @@ def poisson_stream(server: Server, rate: float, duration: float, sizes, accuraci
     rng = np.random.Generator(np.random.PCG64(seed))
     t0 = time.monotonic()
     t = 0.0
-    reqs = []
+    keys = []
+    outstanding = [0]
+    cv = threading.Condition()
+
+    def finished(fut):
+        fut.result()  # raise here if the solve failed; the result itself is dropped
+        with cv:
+            outstanding[0] -= 1
+            cv.notify_all()
+
     while t < warmup + duration:
         n = int(sizes[rng.integers(len(sizes))])
         acc = float(accuracies[rng.integers(len(accuracies))])
@@ -270,23 +321,35 @@ def poisson_stream(server: Server, rate: float, duration: float, sizes, accuraci
         now = time.monotonic()
         if due > now:
             time.sleep(due - now)
-        fut = server.submit(densities[key], acc, arrival=due)
-        reqs.append((t, key, fut))
+        with cv:
+            outstanding[0] += 1
+        server.submit(densities[key], acc, arrival=due).add_done_callback(finished)
+        keys.append((t, key))
         t += float(rng.exponential(1.0 / rate))
-    for _, _, fut in reqs:
-        fut.result()
-    return [(t, key) for t, key, _ in reqs if t >= warmup]
+    with cv:
+        cv.wait_for(lambda: outstanding[0] == 0)
+    return [(t, key) for t, key in keys if t >= warmup]
+
+
+def percentile(sorted_values, p: float):
+    """Nearest-rank percentile of an ascending list."""
+    return sorted_values[min(len(sorted_values) - 1, max(0, int(math.ceil(p / 100.0 * len(sorted_values))) - 1))]
+
+
+def summarize(completed, t_start: float, t_end: float):
+    """p50/p99/mean latency (ms) and throughput of the completed requests that arrived in
+    [t_start, t_end); throughput counts them over [t_start, last completion]."""
+    sel = [r for r in completed if t_start <= r.arrival < t_end]
+    if not sel:
+        return None
+    lat = sorted((r.done_at - r.arrival) * 1e3 for r in sel)
+    span = max(r.done_at for r in sel) - t_start
+    return {"requests": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "mean_ms": sum(lat) / len(lat), "solves_per_s": len(lat) / span}
 
 
 def latency_summary(server: Server, t_start: float, t_end: float):
-    """p50/p99 latency (ms) and throughput of the requests that arrived in [t_start, t_end)."""
-    lat = sorted((r.done_at - r.arrival) * 1e3 for r in server.completed if t_start <= r.arrival < t_end)
-    if not lat:
-        return None
-    span = max(r.done_at for r in server.completed if t_start <= r.arrival < t_end) - t_start
-
-    def pct(p):
-        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
-
-    return {"requests": len(lat), "p50_ms": pct(50), "p99_ms": pct(99), "mean_ms": sum(lat) / len(lat),
-            "solves_per_s": len(lat) / span, "batches": server.batches, "peak_bytes": server.peak_bytes}
+    out = summarize(server.completed, t_start, t_end)
+    if out is not None:
+        out.update({"batches": server.batches, "peak_bytes": server.peak_bytes})
+    return out

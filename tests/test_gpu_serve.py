@@ -1,0 +1,65 @@
+"""Continuous batching: requests of mixed grid sizes and accuracies, admitted while
+others run, give the same result as the same solve alone; the device-memory budget
+bounds what the server holds; an invalid request fails alone."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2506_04489_gb300 import Plan, serve, workloads as W  # noqa: E402
+
+SIZES = (32, 64, 96)
+
+
+def _density(n, seed, precision):
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    return torch.from_numpy(W.gaussian_mixture(n, -1.0, 1.0, seed)).to(dt).pin_memory()
+
+
+def test_results_in_the_mix_equal_alone():
+    srv = serve.Server(budget_bytes=8e9, max_batch=4, slots=3).start()
+    rng = np.random.default_rng(0)
+    reqs = []
+    for i in range(48):
+        n = int(SIZES[rng.integers(3)])
+        acc = (1e-6, 1e-12)[int(rng.integers(2))]
+        rho = _density(n, i, serve.precision_for(acc))
+        reqs.append((n, acc, rho, srv.submit(rho, acc)))
+        if i % 8 == 7:
+            time.sleep(0.002)  # arrivals in bursts, while earlier batches run
+    results = [f.result(timeout=120) for *_, f in reqs]
+    srv.stop()
+    assert srv.batches < len(reqs)  # some requests shared a launch
+    plans = {}
+    for (n, acc, rho, _), u in zip(reqs, results):
+        key = (n, serve.precision_for(acc))
+        if key not in plans:
+            plans[key] = Plan(n, -1.0, 1.0, precision=key[1])
+        alone = plans[key].solve(rho.cuda()).cpu()
+        assert torch.equal(u, alone), key
+    for p in plans.values():
+        p.close()
+
+
+def test_budget_bounds_resident_plans_and_bad_request_fails_alone():
+    # room for one 96^3 plan only: the 64^3 and 96^3 keys must take turns (eviction)
+    one = serve.entry_bytes(96, "df32", 2)
+    srv = serve.Server(budget_bytes=int(1.1 * one), max_batch=2, slots=2).start()
+    futs = []
+    for i in range(12):
+        n = (64, 96)[i % 2]
+        acc = 1e-12
+        futs.append(srv.submit(_density(n, i, "df32"), acc))
+    bad = srv.submit(torch.zeros((64, 64, 64), dtype=torch.float32).pin_memory(), 1e-12)  # wrong dtype
+    for f in futs:
+        assert f.result(timeout=120).shape[0] in (64, 96)
+    with pytest.raises(ValueError):
+        bad.result(timeout=120)
+    too_big = srv.submit(_density(128, 0, "df32"), 1e-12)
+    with pytest.raises(MemoryError):
+        too_big.result(timeout=120)
+    srv.stop()
+    assert srv.peak_bytes <= int(1.1 * one)

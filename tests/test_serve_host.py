@@ -1,0 +1,52 @@
+"""Host-side logic of the solve server (no GPU): accuracy routing, the memory estimate
+that admission uses, percentiles, and the seeded Poisson arrivals."""
+import types
+
+import numpy as np
+
+from paper_2506_04489_gb300 import serve
+
+
+def test_accuracy_routing():
+    assert serve.precision_for(1e-6) == "fp32"
+    assert serve.precision_for(1e-5) == "fp32"
+    assert serve.precision_for(1e-12) == "df32"
+    assert serve.precision_for(1e-9) == "df32"
+
+
+def test_entry_bytes_counts_workspace_and_buffers():
+    # double-float 256^3, batch 8: workspace 8 * 16 * 256 * 512 * 264 B dominates
+    b = serve.entry_bytes(256, "df32", 8)
+    work = 8 * 16 * 256 * 512 * 264
+    io = 2 * 8 * 256 ** 3 * 8
+    assert work + io < b < work + io + 400e6
+    assert serve.entry_bytes(256, "fp32", 8) < b
+    assert serve.entry_bytes(128, "df32", 8) < b / 6
+
+
+def test_percentiles_nearest_rank():
+    v = list(range(1, 101))
+    assert serve.percentile(v, 50) == 50
+    assert serve.percentile(v, 99) == 99
+    assert serve.percentile([7.0], 99) == 7.0
+
+
+def test_summarize_window_and_throughput():
+    reqs = [types.SimpleNamespace(arrival=t, done_at=t + 0.002 * (1 + i % 3)) for i, t in enumerate(np.arange(0, 1, 0.01))]
+    s = serve.summarize(reqs, 0.5, 1.0)
+    assert s["requests"] == 50
+    assert 2.0 <= s["p50_ms"] <= 6.0 and s["p99_ms"] <= 6.0 + 1e-9
+    assert 90 < s["solves_per_s"] < 110
+
+
+def test_poisson_arrivals_are_seeded():
+    # the same seed gives the same sizes, accuracies and inter-arrival gaps
+    def draw(seed):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        out = []
+        for _ in range(20):
+            out.append((int(rng.integers(6)), int(rng.integers(2)), float(rng.exponential(1 / 200))))
+        return out
+    assert draw(0) == draw(0) and draw(0) != draw(1)
+    gaps = [g for _, _, g in draw(0)]
+    assert 0 < np.mean(gaps) < 0.02
