@@ -88,6 +88,18 @@ sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
                          int max_batch);
 
 /*
+ * sp_plan_set_kernel -- which convolution kernel sp_kernel_precompute builds (default
+ * SP_KERNEL_SUPERPOTENTIAL).  SP_KERNEL_GS_PLAIN is the original GS method without its
+ * near-field correction (Sec. 1; the bracketed columns of Tab. 2): the multiplier is the
+ * Fourier transform of the GS approximation of 1/(4 pi |y|) itself, sum_s 2 w_s G1 G2 G3
+ * / Ntilde, with no Laplacian symbol; its cutoff error is O(eps^2) where the
+ * super-potential kernel's is O(eps^4) (Lemma 1).  Marks the plan not ready: call
+ * sp_kernel_precompute afterwards.
+ */
+typedef enum { SP_KERNEL_SUPERPOTENTIAL = 0, SP_KERNEL_GS_PLAIN = 1 } sp_kernel;
+sp_status sp_plan_set_kernel(sp_plan plan, sp_kernel kind);
+
+/*
  * sp_kernel_precompute -- Alg. 1 on the GPU, all in FP64: GS table (if not given),
  * the 1D integral tables G, H of eq. (Gten_sep) (closed full-line forms where
  * a_s L^2 >= 40; else composite 16-point Gauss-Legendre with nodes computed on the

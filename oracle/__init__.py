@@ -66,6 +66,8 @@ def lib():
             L.or_axis_tables.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
             L.or_multiplier.restype = ctypes.c_int
             L.or_multiplier.argtypes = [_ip, _dp, ctypes.c_int, _dp, _dp, _dp]
+            L.or_multiplier_gs_plain.restype = ctypes.c_int
+            L.or_multiplier_gs_plain.argtypes = [_ip, _dp, ctypes.c_int, _dp, _dp, _dp]
             L.or_fft.restype = ctypes.c_int
             L.or_fft.argtypes = [ctypes.c_int, _dp, ctypes.c_int]
             L.or_fft3.restype = ctypes.c_int
@@ -174,10 +176,27 @@ def multiplier(n, L, w: np.ndarray, a: np.ndarray) -> np.ndarray:
     return M
 
 
-def plan_tables(n, lo, hi, eps: float = 1e-4, h_tau: float = 0.1, eta: float = 1e-17):
-    """GS table and multiplier for a box, with the default GS range (eps, |L|]."""
+def multiplier_gs_plain(n, L, w: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """M[k] = sum_s 2 w_s G0 G1 G2: the original GS method without near-field correction."""
+    n = _vec3(n)
+    L = _vec3(L)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    M = np.empty((n[0] + 1, n[1] + 1, n[2] + 1))
+    Lc = (ctypes.c_double * 3)(*[float(x) for x in L])
+    if lib().or_multiplier_gs_plain(_i3(n), Lc, len(w), _d(w), _d(a), _d(M)) != 0:
+        raise MemoryError("or_multiplier_gs_plain")
+    return M
+
+
+def plan_tables(n, lo, hi, eps: float = 1e-4, h_tau: float = 0.1, eta: float = 1e-17, kernel: str = "superpotential"):
+    """GS table and multiplier for a box, with the default GS range (eps, |L|].
+    kernel: "superpotential" (eq. convtheorem) or "gs_plain" (the original GS method
+    without near-field correction)."""
     _, L = geometry(n, lo, hi)
     w, a = gs_table(eps, default_delta(L), h_tau, eta)
+    if kernel == "gs_plain":
+        return w, a, multiplier_gs_plain(_vec3(n), L, w, a)
     return w, a, multiplier(_vec3(n), L, w, a)
 
 

@@ -358,6 +358,48 @@ int or_multiplier(const int n[3], const double L[3], int terms,
     return 0;
 }
 
+/*
+ * Multiplier of the original GS method without its near-field correction (Sec. 1
+ * and the bracketed columns of Tab. 2): the convolution with the GS approximation of
+ * the Newton kernel itself, U(y) = 1/(4 pi |y|) ~ sum_s 2 w_s exp(-a_s |y|^2) (twice the
+ * 1/(8 pi |y|) table of eq. sin_1_x), with no Laplacian symbol:
+ *     M(k) = sum_s 2 w_s G0 G1 G2.
+ * Same storage as or_multiplier.
+ */
+int or_multiplier_gs_plain(const int n[3], const double L[3], int terms,
+                           const double* w, const double* a, double* M)
+{
+    double* G[3];
+    double* H[3];
+    for (int p = 0; p < 3; ++p) {
+        int same = -1;
+        for (int q = 0; q < p; ++q)
+            if (n[q] == n[p] && L[q] == L[p]) { same = q; break; }
+        if (same >= 0) { G[p] = G[same]; H[p] = H[same]; continue; }
+        G[p] = (double*)malloc(sizeof(double) * (size_t)terms * (n[p] + 1));
+        H[p] = (double*)malloc(sizeof(double) * (size_t)terms * (n[p] + 1));
+        if (!G[p] || !H[p]) return -1;
+        or_axis_tables(n[p], L[p], terms, a, G[p], H[p]);
+    }
+    int n1 = n[1] + 1, n2 = n[2] + 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k0 = 0; k0 <= n[0]; ++k0)
+        for (int k1 = 0; k1 <= n[1]; ++k1)
+            for (int k2 = 0; k2 <= n[2]; ++k2) {
+                double v = 0.0;
+                for (int s = 0; s < terms; ++s)
+                    v += 2.0 * w[s] * G[0][s * (n[0] + 1) + k0] * G[1][s * n1 + k1] * G[2][s * n2 + k2];
+                M[((size_t)k0 * n1 + k1) * n2 + k2] = v;
+            }
+    for (int p = 0; p < 3; ++p) {
+        int owner = 1;
+        for (int q = 0; q < p; ++q)
+            if (G[q] == G[p]) owner = 0;
+        if (owner) { free(G[p]); free(H[p]); }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Own FFT: recursive mixed radix, any length (radix 2, 3, else direct DFT)   */
 /* ------------------------------------------------------------------------- */

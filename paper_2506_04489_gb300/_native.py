@@ -51,6 +51,8 @@ lib.sp_plan_set_timing.restype = ctypes.c_int
 lib.sp_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_pass_times.restype = ctypes.c_int
 lib.sp_plan_pass_times.argtypes = [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
+lib.sp_plan_set_kernel.restype = ctypes.c_int
+lib.sp_plan_set_kernel.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_autotune.restype = ctypes.c_int
 lib.sp_plan_autotune.argtypes = [_vp, ctypes.c_int, _vp]
 lib.sp_plan_tiles.restype = ctypes.c_int

@@ -188,6 +188,17 @@ extern "C" sp_status sp_kernel_precompute(sp_plan p, sp_stream stream)
     return SP_OK;
 }
 
+extern "C" sp_status sp_plan_set_kernel(sp_plan p, sp_kernel kind)
+{
+    g_err[0] = 0;
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (kind != SP_KERNEL_SUPERPOTENTIAL && kind != SP_KERNEL_GS_PLAIN)
+        return sp_fail(SP_ERR_INVALID, "unknown kernel %d", (int)kind);
+    p->kernel = (int)kind;
+    p->ready = false;
+    return SP_OK;
+}
+
 static sp_status check_solve_args(sp_plan p, const void* rho, const void* u)
 {
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");

@@ -158,12 +158,13 @@ template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 // slot per butterfly and add compile-time offsets for the others.
 
 // Per-stage twiddle tables in shared memory: stage s (span P > 1, radix RAD) keeps
-// w^{r k N/(P RAD)} at [k RAD + r], so a butterfly reads RAD - 1 consecutive entries.
+// w^{r k N/(P RAD)} at [k (RAD + 1) + r], so a butterfly reads RAD - 1 consecutive
+// entries; the extra entry per row puts the rows of neighbouring k on different banks.
 template <int N, bool INV> constexpr int tw_stage_offset(int s)
 {
     int off = 0;
     for (int i = 0; i < s; ++i)
-        if (span_at<N, INV>(i) > 1) off += span_at<N, INV>(i) * radix_at<N, INV>(i);
+        if (span_at<N, INV>(i) > 1) off += span_at<N, INV>(i) * (radix_at<N, INV>(i) + 1);
     return off;
 }
 template <int N> constexpr int tw_stage_size()
@@ -183,7 +184,7 @@ SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int ti
             cpx<R>* dst = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST);
             for (int j = tid; j < P * RAD; j += nthreads) {
                 const int k = j / RAD, r = j % RAD;
-                dst[j] = tw[r * k * TWS];
+                dst[k * (RAD + 1) + r] = tw[r * k * TWS];
             }
         }
         fill_stage_twiddles<R, N, INV, ST + 1>(tws, tw, tid, nthreads);
@@ -217,7 +218,7 @@ template <class R, int N, bool INV, int ST> struct Stage {
         for (int m = 0; m < NB; ++m) {
             if constexpr (P > 1) {
                 const int k = (t + T * m) % P;
-                const cpx<R>* w = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST) + k * RAD;
+                const cpx<R>* w = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST) + k * (RAD + 1);
 #pragma unroll
                 for (int r = 1; r < RAD; ++r)
                     v[m * RAD + r] = S < 0 ? tw_mul(v[m * RAD + r], w[r]) : tw_mulc(v[m * RAD + r], w[r]);

@@ -47,6 +47,7 @@ struct sp_plan_s {
     size_t work_bytes;
     bool ready;
     int device;
+    int kernel;      // sp_kernel
     // tiles of the register-resident passes (0 = built-in default): columns per CTA of
     // the line passes per axis, pairs of real lines per CTA of the z passes
     int tile_line[3];

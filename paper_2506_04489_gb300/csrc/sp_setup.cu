@@ -245,6 +245,27 @@ __global__ void k_mult_lhs(int row0, int rows, int S, int n0p, int n1p, const do
     Ap[idx] = c < S ? w[s] * (h0 * g1 + g0 * h1) : w[s] * (g0 * g1);
 }
 
+// Original GS method without near-field correction: A'[row][s] = 2 w_s G0 G1 (the GS of
+// 1/(4 pi r) is twice the 1/(8 pi r) table), B'[kz][s] = G2: V = sum_s 2 w_s G0 G1 G2.
+__global__ void k_plain_lhs(int row0, int rows, int S, int n0p, int n1p, const double* w,
+                            const double* G0, const double* G1, double* Ap)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)rows * S) return;
+    int r = (int)(idx / S), s = (int)(idx % S);
+    int row = row0 + r;
+    int k1 = row / n0p, k0 = row % n0p;
+    Ap[idx] = 2.0 * w[s] * G0[(long long)s * n0p + k0] * G1[(long long)s * n1p + k1];
+}
+
+__global__ void k_plain_rhs(int S, int n2p, const double* G2, double* Bp)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n2p * S) return;
+    int kz = (int)(idx / S), s = (int)(idx % S);
+    Bp[idx] = G2[(long long)s * n2p + kz];
+}
+
 // B'[kz][c]: c < S: G2[c][kz], c >= S: H2[c-S][kz]
 __global__ void k_mult_rhs(int S, int n2p, const double* G2, const double* H2, double* Bp)
 {
@@ -254,17 +275,18 @@ __global__ void k_mult_rhs(int S, int n2p, const double* G2, const double* H2, d
     Bp[idx] = c < S ? G2[(long long)c * n2p + kz] : H2[(long long)(c - S) * n2p + kz];
 }
 
-struct EpiMultiplier {  // M[row][kz] = -(kappa0^2 + kappa1^2 + kappa2^2) V / Ntilde
+struct EpiMultiplier {  // M[row][kz] = -(kappa0^2 + kappa1^2 + kappa2^2) V / Ntilde (or V / Ntilde)
     double* M;
     int ldz, row0, n0p;
     double c0, c1, c2;  // (pi / L_p)^2
     double invN;
+    int laplacian;      // 1: super-potential (spectral Laplacian applied); 0: plain GS kernel
     __device__ void operator()(int m, int n, double v) const
     {
         int row = row0 + m;
         int k1 = row / n0p, k0 = row % n0p;
         double k2sum = c0 * (double)k0 * k0 + c1 * (double)k1 * k1 + c2 * (double)n * n;
-        M[(long long)row * ldz + n] = -k2sum * v * invN;
+        M[(long long)row * ldz + n] = laplacian ? -k2sum * v * invN : v * invN;
     }
 };
 
@@ -391,10 +413,15 @@ sp_status sp_setup_run(sp_plan p, cudaStream_t st)
         const int n0p = p->n[0] + 1, n1p = p->n[1] + 1, n2p = p->n[2] + 1;
         const long long rows_total = (long long)n0p * n1p;
         const int chunk = (int)(rows_total < 8192 ? rows_total : 8192);
+        const bool plain = p->kernel == SP_KERNEL_GS_PLAIN;
+        const int K = plain ? S : 2 * S;  // contraction length (GS columns)
         DevBuf Ap(st), Bp(st);
-        if (Ap.alloc(sizeof(double) * (size_t)chunk * 2 * S) || Bp.alloc(sizeof(double) * (size_t)n2p * 2 * S))
+        if (Ap.alloc(sizeof(double) * (size_t)chunk * K) || Bp.alloc(sizeof(double) * (size_t)n2p * K))
             return sp_fail(SP_ERR_OOM, "setup: multiplier scratch allocation failed");
-        k_mult_rhs<<<nblk((long long)n2p * 2 * S, 256), 256, 0, st>>>(S, n2p, p->d_G[2], p->d_H[2], Bp.d());
+        if (plain)
+            k_plain_rhs<<<nblk((long long)n2p * S, 256), 256, 0, st>>>(S, n2p, p->d_G[2], Bp.d());
+        else
+            k_mult_rhs<<<nblk((long long)n2p * 2 * S, 256), 256, 0, st>>>(S, n2p, p->d_G[2], p->d_H[2], Bp.d());
         EpiMultiplier epi;
         epi.M = p->d_M64;
         epi.ldz = p->ldz;
@@ -403,13 +430,18 @@ sp_status sp_setup_run(sp_plan p, cudaStream_t st)
         epi.c1 = (kPi / p->L[1]) * (kPi / p->L[1]);
         epi.c2 = (kPi / p->L[2]) * (kPi / p->L[2]);
         epi.invN = 1.0 / (8.0 * (double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
+        epi.laplacian = plain ? 0 : 1;
         for (long long r0 = 0; r0 < rows_total; r0 += chunk) {
             int rows = (int)((rows_total - r0) < chunk ? (rows_total - r0) : chunk);
-            k_mult_lhs<<<nblk((long long)rows * 2 * S, 256), 256, 0, st>>>(
-                (int)r0, rows, S, n0p, n1p, p->d_gs_w, p->d_G[0], p->d_H[0], p->d_G[1], p->d_H[1], Ap.d());
+            if (plain)
+                k_plain_lhs<<<nblk((long long)rows * S, 256), 256, 0, st>>>(
+                    (int)r0, rows, S, n0p, n1p, p->d_gs_w, p->d_G[0], p->d_G[1], Ap.d());
+            else
+                k_mult_lhs<<<nblk((long long)rows * 2 * S, 256), 256, 0, st>>>(
+                    (int)r0, rows, S, n0p, n1p, p->d_gs_w, p->d_G[0], p->d_H[0], p->d_G[1], p->d_H[1], Ap.d());
             epi.row0 = (int)r0;
             dim3 grid(nblk(n2p, TN), nblk(rows, TM));
-            k_dgemm_nt<<<grid, 256, 0, st>>>(rows, n2p, 2 * S, Ap.d(), 2 * S, Bp.d(), 2 * S, epi);
+            k_dgemm_nt<<<grid, 256, 0, st>>>(rows, n2p, K, Ap.d(), K, Bp.d(), K, epi);
         }
         long long mcount = rows_total * p->ldz;
         if (p->d_M32) k_to_f32<<<nblk(mcount, 256), 256, 0, st>>>(mcount, p->d_M64, p->d_M32);

@@ -39,10 +39,12 @@ class Plan:
     gs        : optional explicit GS table (weights, exponents) as float64 arrays.
     max_batch : largest batch for ``solve_batched``.
     precompute: run Alg. 1 on the current stream at construction.
+    kernel    : "superpotential" (the paper's method) or "gs_plain" (the original GS
+                method without near-field correction, for comparison).
     """
 
     def __init__(self, n, lo, hi, precision: str = "fp64", eps: float = 1e-4, gs=None,
-                 max_batch: int = 1, precompute: bool = True, stream=None):
+                 max_batch: int = 1, precompute: bool = True, stream=None, kernel: str = "superpotential"):
         from . import _native as N
         self._N = N
         if precision not in _PREC:
@@ -67,6 +69,11 @@ class Plan:
                                      _PREC[precision], self.max_batch), "sp_plan_create")
         self._h = h
         self.dtype = precision_dtype(precision)
+        if kernel not in ("superpotential", "gs_plain"):
+            raise ValueError("kernel must be 'superpotential' or 'gs_plain'")
+        self.kernel = kernel
+        if kernel == "gs_plain":
+            N.check(N.lib.sp_plan_set_kernel(h, 1), "sp_plan_set_kernel")
         if precompute:
             self.precompute(stream)
 

@@ -210,3 +210,15 @@ def test_not_ready_and_batch_errors():
         plan.solve_batched(torch.zeros((3, 8, 8, 8), dtype=torch.float64, device="cuda"))
     assert e.value.status == "SP_ERR_INVALID"
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df32", "fp32"])
+def test_plain_gs_kernel_matches_oracle(oracle, precision):
+    n, lo, hi = (64, 64, 64), (-2.0,) * 3, (2.0,) * 3
+    rho = W.gaussian(64, -2.0, 2.0, 0.2)
+    _, _, M = oracle.plan_tables(n, lo, hi, kernel="gs_plain")
+    ref = oracle.solve(M, rho)
+    plan = Plan(n, lo, hi, precision=precision, kernel="gs_plain")
+    u = plan.solve(torch.from_numpy(rho).cuda().to(plan.dtype)).double().cpu().numpy()
+    plan.close()
+    assert _rel(u, ref) <= TOL[precision]

@@ -189,3 +189,27 @@ def test_bump_profile_density_radial_quadrature(oracle):
         worst = max(worst, float(np.abs(u[rs == q] - v).max()))
     # the bump is C-infinity but not analytic: 1.2e-7 at n = 64 on [-1,1]^3
     assert worst / umax < 5e-7, worst / umax
+
+
+def _order(eps, E):
+    return math.log(E[0] / E[-1]) / math.log(eps[0] / eps[-1])
+
+
+def test_cutoff_error_orders_superpotential_vs_plain_gs(oracle):
+    # Lemma 1 / Thm. 1: the super-potential kernel's GS cutoff error is O(eps^4); the
+    # original GS method without near-field correction (Tab. 2 brackets) is O(eps^2).
+    # Absolute values depend on the unstated GS generator and eps convention of the
+    # paper's code (Tab. 3 is not reproduced); the orders are.
+    lo, hi, sigma = -2.0, 2.0, 0.2
+    eps = [2.2e-2, 5.7e-3, 1.6e-3]
+    E4 = []
+    for e in eps:
+        _, _, M = oracle.plan_tables(64, lo, hi, eps=e)
+        E4.append(A.rel_err(oracle.solve(M, W.gaussian(64, lo, hi, sigma)), A.gaussian_u(64, lo, hi, sigma)))
+    assert 3.5 <= _order(eps, E4) <= 4.5, E4
+    eps2 = [7.5e-2, 5.7e-3, 4.7e-4]
+    E2 = []
+    for e in eps2:
+        _, _, M = oracle.plan_tables(32, lo, hi, eps=e, kernel="gs_plain")
+        E2.append(A.rel_err(oracle.solve(M, W.gaussian(32, lo, hi, sigma)), A.gaussian_u(32, lo, hi, sigma)))
+    assert 1.7 <= _order(eps2, E2) <= 2.3, E2
