@@ -110,10 +110,12 @@ __device__ __forceinline__ df32 df_dot_add(df32 a, df32 b, df32 c, df32 d)
     return df_make(s, e);
 }
 
-// Renormalise to |lo| <= ulp(hi)/2 (two-sum: no ordering assumption).
+// Renormalise (fast two-sum).  Exact when |hi| >= |lo|; otherwise (hi cancelled to
+// below the accumulated lo) the lost part is a rounding of lo, i.e. a small multiple of
+// 2^-48 of the operands that produced the value: the same form of bound as the sum's.
 __device__ __forceinline__ df32 df_norm(df32 a)
 {
     df32 r;
-    two_sum(a.hi, a.lo, r.hi, r.lo);
+    fast_two_sum(a.hi, a.lo, r.hi, r.lo);
     return r;
 }
