@@ -65,15 +65,20 @@ struct LArgs {
     long long in_os, in_es, in_bs;  // outer / element / batch strides (complex elements)
     long long out_os, out_es, out_bs;
     int ncol;                        // valid columns (kz = 0..n2)
-    int B;                           // columns per CTA (a power of two <= lanes_b_max<N>())
+    int B;                           // columns per CTA (a power of two <= lanes_b_max<R, N>())
     int lgB;                         // log2(B), set by the launcher
     const void* tw;                  // exp(-2 pi i j / N), j < N
     const void* M;                   // XMUL: multiplier [|ko|][|kl|][kz], row stride ldzM
     int No, nh_line, ldzM;
 };
 
-// Largest column tile of a line pass (the launch bound); the runtime tile B divides it.
-template <int N> constexpr int lanes_b_max() { return N >= 1024 ? 8 : 16; }
+// Largest column tile of a line pass (the launch bound of the runtime-tile kernel):
+// 512 threads per CTA for 16-byte complex values (room for 128 registers), 1024 for
+// 8-byte ones.
+template <class R, int N> constexpr int lanes_b_max()
+{
+    return sizeof(cpx<R>) >= 16 ? (N >= 1024 ? 4 : 8) : (N >= 1024 ? 8 : 16);
+}
 template <int N> constexpr int lanes_b_default() { return N >= 1024 ? 4 : 8; }
 
 // Resident CTAs per SM requested from the compiler: 1024 threads per SM (at most 64
@@ -83,11 +88,19 @@ template <int N, int THREADS> constexpr int min_blocks() { return FFTPlan<N>::E 
 
 // LGB >= 0: the tile 2^LGB is a compile-time constant (the default tile); LGB = -1: the
 // tile comes from a.lgB (other tiles chosen by the autotuner).
-template <int N, int LGB> constexpr int line_threads() { return (N / FFTPlan<N>::E) << (LGB >= 0 ? LGB : 4); }
+template <class R, int N> constexpr int lg_max()
+{
+    return lanes_b_max<R, N>() >= 16 ? 4 : (lanes_b_max<R, N>() >= 8 ? 3 : 2);
+}
+template <class R, int N, int LGB> constexpr int line_threads()
+{
+    return (N / FFTPlan<N>::E) << (LGB >= 0 ? LGB : lg_max<R, N>());
+}
 template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
 
 template <class R, int N, int MODE, int LGB>
-__global__ void __launch_bounds__(line_threads<N, LGB>(), min_blocks<N, line_threads<N, LGB>()>()) k2_line(LArgs a)
+__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<N, line_threads<R, N, LGB>()>() : 1)
+    k2_line(LArgs a)
 {
     constexpr int E = FFTPlan<N>::E, T = N / E;
     constexpr int R0 = FFTPlan<N>::R[0];
@@ -122,6 +135,25 @@ __global__ void __launch_bounds__(line_threads<N, LGB>(), min_blocks<N, line_thr
             v[j] = (cv && (j % R0) < R0 / 2) ? in[e * a.in_es] : czero<R>();
         }
     }
+    // x pass, FP32: the multiplier values of this thread's outputs are loaded before the
+    // forward transform, so their latency overlaps its arithmetic (the wider types keep
+    // the registers for the transform and load them after it)
+    constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
+    R mv[MODE == XMUL ? E : 1];
+    const R* M = static_cast<const R*>(a.M);
+    const int ko = o <= a.No / 2 ? o : a.No - o;
+    const long long mrow = (long long)ko * (a.nh_line + 1);
+    if constexpr (PREFETCH_M) {
+        const R* M = static_cast<const R*>(a.M);
+        const int ko = o <= a.No / 2 ? o : a.No - o;
+        const long long mrow = (long long)ko * (a.nh_line + 1);
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int e = last_element<N, false>(t, j);
+            const int ke = e <= N / 2 ? e : N - e;
+            mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
+        }
+    }
     __syncthreads();
     cpx<R>* fresh;
     if constexpr (MODE == INV) {
@@ -130,15 +162,14 @@ __global__ void __launch_bounds__(line_threads<N, LGB>(), min_blocks<N, line_thr
         fresh = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
     }
     if constexpr (MODE == XMUL) {
-        const R* M = static_cast<const R*>(a.M);
-        const int ko = o <= a.No / 2 ? o : a.No - o;
-        const long long mrow = (long long)ko * (a.nh_line + 1);
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = last_element<N, false>(t, j);
-            const int ke = e <= N / 2 ? e : N - e;
-            const R m = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
-            v[j] = scale(v[j], m);
+            if constexpr (!PREFETCH_M) {
+                const int e = last_element<N, false>(t, j);
+                const int ke = e <= N / 2 ? e : N - e;
+                mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
+            }
+            v[j] = scale(v[j], mv[j]);
         }
         run_stages<R, N, true, +1, false>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
     }
@@ -289,7 +320,7 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     LArgs ab = a;
     ab.B = a.B ? a.B : lanes_b_default<N>();
     const int B = ab.B;
-    if (B < 1 || B > lanes_b_max<N>() || (B & (B - 1))) return sp_fail(SP_ERR_INVALID, "bad line tile %d", B);
+    if (B < 1 || B > lanes_b_max<R, N>() || (B & (B - 1))) return sp_fail(SP_ERR_INVALID, "bad line tile %d", B);
     ab.lgB = 0;
     while ((1 << ab.lgB) < B) ++ab.lgB;
     const size_t buf = sizeof(cpx<R>) * LayStrided<R>::size(N, B);
