@@ -40,7 +40,7 @@ template <class R> struct LayStrided {
     SP_D int operator()(int e) const { return (e << lgB) + (((e >> 3) << lgB) & pad_mask) + b; }
     SP_D int unit() const { return 1 << lgB; }
     SP_D int step(int d) const { return (d << lgB) + (((d >> 3) << lgB) & pad_mask); }  // d a multiple of 8
-    static SP_HD int size(int N, int B) { return N * B + (N / 8) * (B * (int)sizeof(cpx<R>) >= 128 ? 0 : B); }
+    static constexpr SP_HD int size(int N, int B) { return N * B + (N / 8) * (B * (int)sizeof(cpx<R>) >= 128 ? 0 : B); }
 };
 // Contiguous lines: lane t is fastest; one padding entry after every 8 entries.
 template <int N> struct LayLine {
@@ -53,7 +53,8 @@ template <int N> struct LayLine {
 
 // Shared memory of a pass: the staged twiddles of the directions it runs, then one or
 // two exchange buffers (two when both fit in 100 KB, for one barrier per stage).
-template <class R, int N> constexpr int tw_entries() { return tw_stage_size<N>(); }
+// (rounded up to an even count, so that everything after it starts on a 16-byte boundary)
+template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<N>() + 1) & ~1; }
 constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 
 // ------------------------------------------------------------------ strided passes
@@ -65,6 +66,7 @@ struct LArgs {
     long long in_os, in_es, in_bs;  // outer / element / batch strides (complex elements)
     long long out_os, out_es, out_bs;
     int ncol;                        // valid columns (kz = 0..n2)
+    int in_ld;                       // columns allocated per input row (>= ncol)
     int B;                           // columns per CTA (a power of two <= lanes_b_max<R, N>())
     int lgB;                         // log2(B), set by the launcher
     const void* tw;                  // exp(-2 pi i j / N), j < N
@@ -182,6 +184,146 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
         for (int j = 0; j < E; ++j)
             if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
     }
+}
+
+// ------------------------------------------------------------------ pipelined line passes
+// Persistent variant of k2_line (default tile only): each CTA walks tiles (batch, outer
+// index, column block) with a stride of gridDim.x.  A tile's input rows (B contiguous
+// complex values each) are copied into a shared-memory stage with cp.async; after the
+// threads have moved the current tile's values from the stage into registers, the copies
+// of the next tile are issued, so they land while the current tile computes.
+SP_D void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+SP_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+SP_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct PArgs {
+    LArgs a;
+    int outer;   // extent of the outer index
+    int ncb;     // column blocks
+    int ntiles;  // batch * outer * ncb
+};
+
+template <class R, int N, int MODE> constexpr int stage_rows() { return MODE == INV ? N : N / 2; }
+template <class R, int N, int MODE> constexpr size_t pipe_smem()
+{
+    constexpr int B = 1 << lg_default<N>();
+    constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
+    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
+    return twb + (two_buffers(buf, twb) ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
+}
+
+template <class R, int N, int MODE>
+__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blocks<N, line_threads<R, N, lg_default<N>()>()>())
+    k3_line(PArgs pa)
+{
+    constexpr int E = FFTPlan<N>::E, T = N / E;
+    constexpr int R0 = FFTPlan<N>::R[0];
+    constexpr int LGB = lg_default<N>(), B = 1 << LGB;
+    constexpr int NIN = stage_rows<R, N, MODE>();
+    constexpr int CH = B * (int)sizeof(cpx<R>) / 16;  // 16-byte chunks per row
+    using Lay = LayStrided<R>;
+    // cp.async writes 16-byte chunks: the stage must start on a 16-byte boundary
+    static_assert((sizeof(cpx<R>) * tw_entries<R, N>()) % 16 == 0, "twiddle area alignment");
+    static_assert((sizeof(cpx<R>) * Lay::size(N, B)) % 16 == 0, "exchange buffer alignment");
+    static_assert((B * sizeof(cpx<R>)) % 16 == 0, "stage row alignment");
+    const LArgs& a = pa.a;
+    const int BUF = Lay::size(N, B);
+    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, sizeof(cpx<R>) * tw_entries<R, N>());
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
+    cpx<R>* stg = sm0 + (DB ? 2 : 1) * BUF;
+    const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> LGB;
+    const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
+    if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws, twg, tid, blockDim.x);
+    if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws, twg, tid, blockDim.x);
+    const Lay lay(LGB, b);
+    auto decode = [&](int tile, int& batch, int& o, int& cb) {
+        cb = tile % pa.ncb;
+        const int r = tile / pa.ncb;
+        o = r % pa.outer;
+        batch = r / pa.outer;
+    };
+    auto issue = [&](int tile) {
+        int batch, o, cb;
+        decode(tile, batch, o, cb);
+        const char* src = reinterpret_cast<const char*>(static_cast<const cpx<R>*>(a.in) + batch * a.in_bs +
+                                                        o * a.in_os + cb * B);
+        for (int q = tid; q < NIN * CH; q += blockDim.x) {
+            const int row = q / CH, ch = q % CH;
+            cp_async16(reinterpret_cast<char*>(stg) + (size_t)row * B * sizeof(cpx<R>) + ch * 16,
+                       src + (long long)row * a.in_es * (long long)sizeof(cpx<R>) + ch * 16);
+        }
+        cp_async_commit();
+    };
+    if (blockIdx.x < pa.ntiles) issue(blockIdx.x);
+    for (int tile = blockIdx.x; tile < pa.ntiles; tile += gridDim.x) {
+        int batch, o, cb;
+        decode(tile, batch, o, cb);
+        const int c = cb * B + b;
+        const bool cv = c < a.ncol;
+        cp_async_wait_all();
+        __syncthreads();  // this tile's rows (and, on the first tile, the twiddles) are in
+        cpx<R> v[E];
+        if constexpr (MODE == INV) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[j] = stg[first_element<N, true>(t, j) * B + b];
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                v[j] = ((j % R0) < R0 / 2) ? stg[first_element<N, false>(t, j) * B + b] : czero<R>();
+        }
+        constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
+        R mv[MODE == XMUL ? E : 1];
+        const R* M = static_cast<const R*>(a.M);
+        const int ko = o <= a.No / 2 ? o : a.No - o;
+        const long long mrow = (long long)ko * (a.nh_line + 1);
+        if constexpr (PREFETCH_M) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int e = last_element<N, false>(t, j);
+                const int ke = e <= N / 2 ? e : N - e;
+                mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
+            }
+        }
+        __syncthreads();  // the stage is free: start the next tile's copies
+        if (tile + (int)gridDim.x < pa.ntiles) issue(tile + gridDim.x);
+        cpx<R>* fresh;
+        if constexpr (MODE == INV) {
+            fresh = run_stages<R, N, true, +1, false>(v, sm0, sm1, lay, tws, t);
+        } else {
+            fresh = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
+        }
+        if constexpr (MODE == XMUL) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                if constexpr (!PREFETCH_M) {
+                    const int e = last_element<N, false>(t, j);
+                    const int ke = e <= N / 2 ? e : N - e;
+                    mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
+                }
+                v[j] = scale(v[j], mv[j]);
+            }
+            run_stages<R, N, true, +1, false>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
+        }
+        cpx<R>* out = static_cast<cpx<R>*>(a.out) + batch * a.out_bs + o * a.out_os + c;
+        if constexpr (MODE == FWD) {
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if (cv) out[last_element<N, false>(t, j) * a.out_es] = norm(v[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
+        }
+        __syncthreads();  // exchange buffers free before the next tile's first write
+    }
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ z passes
@@ -328,7 +470,32 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf;
     dim3 grid((unsigned)((a.ncol + B - 1) / B), (unsigned)outer, (unsigned)batch);
     sp_status rc;
-    if (ab.lgB == lg_default<N>()) {
+    constexpr size_t psmem = pipe_smem<R, N, MODE>();
+    // pipelined persistent kernel: default tile, inputs whose rows are 16-byte aligned
+    // (the workspace), and a stage that still leaves two CTAs per SM
+    const bool rows_aligned = ((uintptr_t)a.in % 16 == 0) && (a.in_es * sizeof(cpx<R>)) % 16 == 0 &&
+                              (a.in_os * sizeof(cpx<R>)) % 16 == 0 && (a.in_bs * sizeof(cpx<R>)) % 16 == 0;
+    if (ab.lgB == lg_default<N>() && psmem <= 110 * 1024 && rows_aligned && (a.ncol + B - 1) / B * B <= a.in_ld) {
+        if ((rc = smem_attr<k3_line<R, N, MODE>>(psmem))) return rc;
+        static int per_sm = 0;
+        if (!per_sm) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_line<R, N, MODE>, (N / E) * B, psmem);
+            if (per_sm < 1) per_sm = 1;
+            (void)sms;
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        PArgs pa;
+        pa.a = ab;
+        pa.outer = outer;
+        pa.ncb = (a.ncol + B - 1) / B;
+        pa.ntiles = batch * outer * pa.ncb;
+        const int nblocks = pa.ntiles < per_sm * sms ? pa.ntiles : per_sm * sms;
+        k3_line<R, N, MODE><<<nblocks, (N / E) * B, psmem, st>>>(pa);
+    } else if (ab.lgB == lg_default<N>()) {
         if ((rc = smem_attr<k2_line<R, N, MODE, lg_default<N>()>>(smem))) return rc;
         k2_line<R, N, MODE, lg_default<N>()><<<grid, (N / E) * B, smem, st>>>(ab);
     } else {
@@ -433,6 +600,7 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     y.in_es = y.out_es = p->ldz;
     y.in_bs = y.out_bs = (long long)p->n[0] * p->plane;
     y.ncol = p->n[2] + 1;
+    y.in_ld = p->ldz;
     y.tw = Tabs<R>::tw(p, 1);
     y.B = p->tile_line[1];
     LArgs x = y;
@@ -484,6 +652,7 @@ float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_
     y.in_es = y.out_es = p->ldz;
     y.in_bs = y.out_bs = (long long)p->n[0] * p->plane;
     y.ncol = p->n[2] + 1;
+    y.in_ld = p->ldz;
     y.tw = Tabs<R>::tw(p, 1);
     y.B = tile;
     LArgs x = y;
@@ -542,6 +711,7 @@ sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
     y.in_os = y.out_os = p->plane;
     y.in_es = y.out_es = p->ldz;
     y.ncol = p->n[2] + 1;
+    y.in_ld = p->ldz;
     y.tw = Tabs<R>::tw(p, 1);
     y.B = p->tile_line[1];
     LArgs x = y;
