@@ -174,6 +174,48 @@ class Plan:
                       "sp_graph_capture")
         return Graph(self, g, (rho, out))
 
+    def solve_host_stream(self, inputs, outputs, stream=None):
+        """Solve a sequence of CPU densities into CPU outputs (pinned tensors of the plan's
+        shape and dtype), overlapping the host-to-device copy of input i+1 and the
+        device-to-host copy of result i-1 with the solve of i.  The solves run in order
+        on ``stream`` (the plan has one workspace); each copy direction has a stream of
+        its own, two device buffers per direction.  Returns after the last result is on
+        the host."""
+        import torch
+        solve_st = stream if stream is not None else torch.cuda.current_stream()
+        if getattr(self, "_copy_streams", None) is None:
+            self._copy_streams = (torch.cuda.Stream(), torch.cuda.Stream())
+            self._stream_bufs = [torch.empty(self.n, dtype=self.dtype, device="cuda") for _ in range(4)]
+        h2d, d2h = self._copy_streams
+        dev_in, dev_out = self._stream_bufs[:2], self._stream_bufs[2:]
+        h2d.wait_stream(torch.cuda.current_stream())  # buffers made on the current stream
+        d2h.wait_stream(torch.cuda.current_stream())
+        n = len(inputs)
+        loaded = [torch.cuda.Event() for _ in range(2)]
+        solved = [torch.cuda.Event() for _ in range(2)]
+        fetched = [torch.cuda.Event() for _ in range(2)]
+        for i in range(n + 1):
+            if i < n:  # input i, once solve i-2 has released its buffer
+                k = i % 2
+                if i >= 2:
+                    h2d.wait_event(solved[k])
+                with torch.cuda.stream(h2d):
+                    dev_in[k].copy_(inputs[i], non_blocking=True)
+                    loaded[k].record(h2d)
+            if i >= 1:  # solve i-1 once its input is in and result i-3 is out
+                j = (i - 1) % 2
+                solve_st.wait_event(loaded[j])
+                if i - 1 >= 2:
+                    solve_st.wait_event(fetched[j])
+                self.solve(dev_in[j], dev_out[j], solve_st)
+                solved[j].record(solve_st)
+                d2h.wait_event(solved[j])
+                with torch.cuda.stream(d2h):
+                    outputs[i - 1].copy_(dev_out[j], non_blocking=True)
+                    fetched[j].record(d2h)
+        d2h.synchronize()
+        return outputs
+
     # ----------------------------------------------------------------- diagnostics
     def set_timing(self, enable: bool) -> None:
         self._N.check(self._N.lib.sp_plan_set_timing(self._h, int(bool(enable))), "sp_plan_set_timing")

@@ -79,24 +79,35 @@ class _Entry:
         self.last_used = time.monotonic()
 
 
+def batch_cap(n: int, max_batch: int, max_points: int) -> int:
+    """Requests of an n^3 grid per launch: at most max_batch, at most max_points grid
+    points, and always at least one."""
+    return max(1, min(int(max_batch), int(max_points) // n ** 3))
+
+
 class Server:
     """Continuous-batching server for solves on the box [lo, hi]^3.
 
     budget_bytes  : device memory the server may hold (plans + batch buffers).
     max_batch     : largest batch per launch.
+    max_batch_points : largest number of grid points per launch (batch x n^3); a batch of
+                    large grids is cut at this size so a request queued behind it waits for
+                    a bounded amount of work, not for max_batch full-size solves.
     slots         : concurrent batches (CUDA streams).
     plans_per_key : resident plans per (n, precision); further requests of a busy key wait
                     and are batched together when a plan frees up.
     """
 
     def __init__(self, lo: float = -1.0, hi: float = 1.0, budget_bytes: float = 120e9, max_batch: int = 8,
-                 slots: int = 4, device: int = 0, plans_per_key: int = 2):
+                 slots: int = 4, device: int = 0, plans_per_key: int = 2,
+                 max_batch_points: int = 2 * 256 ** 3):
         import torch
         self.torch = torch
         self.plans_per_key = int(plans_per_key)
         self.lo, self.hi = float(lo), float(hi)
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
+        self.max_batch_points = int(max_batch_points)
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.slot_busy = [None] * slots  # (event, entry, [(request, host_out)])
@@ -267,7 +278,8 @@ class Server:
                     continue
                 with self._lock:
                     q = self.pending[key]
-                    reqs = [q.popleft() for _ in range(min(self.max_batch, len(q)))]
+                    cap = batch_cap(key[0], self.max_batch, self.max_batch_points)
+                    reqs = [q.popleft() for _ in range(min(cap, len(q)))]
                 entry.busy = True
                 self._launch(free[0], entry, reqs)
                 launched = started = True

@@ -67,3 +67,23 @@ def test_autotune_keeps_results_bitwise(oracle):
     after = plan.solve_batched(rho)
     assert torch.equal(before, after)
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["df32", "fp32"])
+def test_host_stream_matches_device_solves(rhs, precision):
+    # overlapped host->device->host solves give the same bits as device-resident solves,
+    # for a sequence longer than the two staging buffers and with repeated host buffers
+    plan = Plan(N, LO, HI, precision=precision)
+    k = 7
+    ins = [rhs[b].to(dtype=plan.dtype).pin_memory() for b in range(k)]
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    plan.solve_host_stream(ins, outs)
+    for b in range(k):
+        want = plan.solve(ins[b].cuda()).cpu()
+        assert torch.equal(outs[b], want), b
+    # one input buffer reused for every step, fresh outputs
+    outs2 = [torch.empty_like(ins[0]).pin_memory() for _ in range(3)]
+    plan.solve_host_stream([ins[2]] * 3, outs2)
+    for o in outs2:
+        assert torch.equal(o, outs[2])
+    plan.close()

@@ -50,3 +50,12 @@ def test_poisson_arrivals_are_seeded():
     assert draw(0) == draw(0) and draw(0) != draw(1)
     gaps = [g for _, _, g in draw(0)]
     assert 0 < np.mean(gaps) < 0.02
+
+
+def test_batch_cap_by_points():
+    # 256^3 grids: two per launch under a 2 x 256^3 point cap; small grids up to max_batch
+    assert serve.batch_cap(256, 8, 2 * 256 ** 3) == 2
+    assert serve.batch_cap(128, 8, 2 * 256 ** 3) == 8
+    assert serve.batch_cap(64, 8, 2 * 256 ** 3) == 8
+    # a grid larger than the cap still runs, alone
+    assert serve.batch_cap(512, 8, 2 * 256 ** 3) == 1
