@@ -50,7 +50,7 @@ typedef enum {
 typedef enum {
     SP_OK = 0,
     SP_ERR_INVALID = 1,          /* bad argument (null pointer, bad box, ...)          */
-    SP_ERR_UNSUPPORTED_SIZE = 2, /* n < 2, or 2n has a prime factor other than 2 and 3 */
+    SP_ERR_UNSUPPORTED_SIZE = 2, /* n < 2, 2n > 2048, or 2n has a prime factor above 7  */
     SP_ERR_OOM = 3,              /* device allocation failed                            */
     SP_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed         */
     SP_ERR_TIMEOUT = 5,          /* a bounded device wait gave up                       */
@@ -64,8 +64,9 @@ typedef void* sp_stream; /* a cudaStream_t */
  * sp_plan_create -- validate the problem and allocate the plan's device memory
  * (Alg. 1 inputs).
  *   out        : receives the plan handle (set to NULL on failure).
- *   n[3]       : grid points per axis, each >= 2 with 2n a product of 2s and 3s
- *                (the padded FFT lengths), 2n <= 4096.
+ *   n[3]       : grid points per axis, each >= 2 with 2n a product of 2s, 3s, 5s and
+ *                7s (the padded FFT lengths, transformed by radix 2/3/4/5/7/8
+ *                stages), 2n <= 2048.
  *   box_lo/hi  : box faces per axis, hi > lo (the grid spans them inclusively).
  *   padding    : must be 2 (the paper's padding factor, Alg. 1).
  *   gs_w, gs_a : host arrays of gs_terms GS weights/exponents (eq. sin_1_x), copied;

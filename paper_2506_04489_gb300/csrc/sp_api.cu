@@ -31,11 +31,12 @@ sp_status sp_cuda_check(cudaError_t e, const char* what)
                    cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-static bool smooth23(int m)
+// Padded lengths the radix-2/3/4/5/7/8 passes can transform: products of 2, 3, 5 and 7.
+static bool smooth2357(int m)
 {
     if (m < 2) return false;
-    while (m % 2 == 0) m /= 2;
-    while (m % 3 == 0) m /= 3;
+    for (int f : {2, 3, 5, 7})
+        while (m % f == 0) m /= f;
     return m == 1;
 }
 
@@ -85,10 +86,10 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
         return sp_fail(SP_ERR_INVALID, "unknown precision %d", (int)prec);
     if (max_batch < 1) return sp_fail(SP_ERR_INVALID, "max_batch must be >= 1 (got %d)", max_batch);
     for (int ax = 0; ax < 3; ++ax) {
-        if (n[ax] < 2 || !smooth23(2 * n[ax]) || 2 * n[ax] > kMaxLen)
+        if (n[ax] < 2 || !smooth2357(2 * n[ax]) || 2 * n[ax] > kMaxLen)
             return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
-                           "n[%d] = %d: need n >= 2 and 2n a product of 2s and 3s, 2n <= %d", ax, n[ax],
-                           kMaxLen);
+                           "n[%d] = %d: need n >= 2 and 2n a product of 2s, 3s, 5s and 7s, 2n <= %d", ax,
+                           n[ax], kMaxLen);
         if (prec == SP_DF32 && !sp_v2_supported(2 * n[ax]))
             return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
                            "n[%d] = %d: double-float passes need 2n in {64, 128, 192, 256, 384, 512, 1024}", ax,

@@ -91,12 +91,69 @@ template <int S, class R> SP_D void dft8(cpx<R>* u)
     u[7] = e[3] - o3;
 }
 
+// Odd prime length P: with t_j = u_j + u_{P-j}, v_j = u_j - u_{P-j} (j = 1..H, H = (P-1)/2),
+//   X[q]   = u_0 + sum_j t_j cos(2 pi jq/P) + S i sum_j v_j sin(2 pi jq/P)
+//   X[P-q] = u_0 + sum_j t_j cos(2 pi jq/P) - S i sum_j v_j sin(2 pi jq/P),  q = 1..H.
+// c[m], s[m] hold cos and sin of 2 pi m / P for m = 0..H; jq mod P is folded into that
+// range by the symmetry of cos (even) and sin (odd) about P/2.
+template <int S, int P, class R> SP_D void dft_odd(cpx<R>* u, const R* c, const R* s)
+{
+    constexpr int H = (P - 1) / 2;
+    cpx<R> t[H + 1], v[H + 1];
+    cpx<R> sum = u[0];
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+        t[j] = u[j] + u[P - j];
+        v[j] = u[j] - u[P - j];
+        sum = sum + t[j];
+    }
+    cpx<R> out[P];
+    out[0] = sum;
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+        cpx<R> a = u[0], b = mk(R(0), R(0));
+#pragma unroll
+        for (int j = 1; j <= H; ++j) {
+            const int m = (j * q) % P;
+            const R cm = m <= H ? c[m] : c[P - m];
+            const R sm = m <= H ? s[m] : -s[P - m];
+            a = mk(a.re + cm * t[j].re, a.im + cm * t[j].im);
+            b = mk(b.re + sm * v[j].re, b.im + sm * v[j].im);
+        }
+        const cpx<R> w = mul_si<S>(b);
+        out[q] = a + w;
+        out[P - q] = a - w;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) u[q] = out[q];
+}
+
+template <int S, class R> SP_D void dft5(cpx<R>* u)
+{
+    // cos and sin of 2 pi m / 5, m = 0, 1, 2
+    const R c[3] = {R(1), R(0.309016994374947424102293417182819059), R(-0.809016994374947424102293417182819059)};
+    const R s[3] = {R(0), R(0.951056516295153572116439333379382143), R(0.587785252292473129168705954639072769)};
+    dft_odd<S, 5>(u, c, s);
+}
+
+template <int S, class R> SP_D void dft7(cpx<R>* u)
+{
+    // cos and sin of 2 pi m / 7, m = 0..3
+    const R c[4] = {R(1), R(0.623489801858733530525004884004239811), R(-0.222520933956314404288902564496794759),
+                    R(-0.900968867902419126236102319507445051)};
+    const R s[4] = {R(0), R(0.78183148246802980870844452667405775), R(0.974927912181823607018131682993931217),
+                    R(0.433883739117558120475768332848358755)};
+    dft_odd<S, 7>(u, c, s);
+}
+
 template <int S, class R> SP_D void dft_small(int radix, cpx<R>* u)
 {
     switch (radix) {
         case 2: dft2<S>(u); break;
         case 3: dft3<S>(u); break;
         case 4: dft4<S>(u); break;
+        case 5: dft5<S>(u); break;
+        case 7: dft7<S>(u); break;
         case 8: dft8<S>(u); break;
         default: break;
     }
@@ -109,18 +166,24 @@ struct RadixPlan {
     int r[SP_MAX_STAGES];
 };
 
-// Factor N (a product of 2s and 3s) into stages, largest radices first: 8s, then a 4
-// or 2 for the remaining power of two, then 3s.  Returns false for other lengths.
+// Factor N (a product of 2s, 3s, 5s and 7s) into stages, largest power-of-two radices
+// first: 8s, then a 4 or 2 for the remaining power of two, then 3s, 5s and 7s.  Returns
+// false for other lengths.
 static inline bool sp_radix_plan(int N, RadixPlan* p)
 {
     p->nst = 0;
-    int m = N, twos = 0, threes = 0;
+    int m = N, twos = 0, threes = 0, fives = 0, sevens = 0;
     while (m % 2 == 0) { m /= 2; ++twos; }
     while (m % 3 == 0) { m /= 3; ++threes; }
+    while (m % 5 == 0) { m /= 5; ++fives; }
+    while (m % 7 == 0) { m /= 7; ++sevens; }
     if (m != 1 || N < 2) return false;
+    if (twos / 3 + (twos % 3 != 0) + threes + fives + sevens > SP_MAX_STAGES) return false;
     while (twos >= 3) { p->r[p->nst++] = 8; twos -= 3; }
     if (twos == 2) p->r[p->nst++] = 4;
     if (twos == 1) p->r[p->nst++] = 2;
     for (int i = 0; i < threes; ++i) p->r[p->nst++] = 3;
-    return p->nst <= SP_MAX_STAGES;
+    for (int i = 0; i < fives; ++i) p->r[p->nst++] = 5;
+    for (int i = 0; i < sevens; ++i) p->r[p->nst++] = 7;
+    return true;
 }

@@ -61,6 +61,10 @@ CASES = [
     ((64, 48, 36), (-2, -2, -2), (2, 2, 2)),
     ((96, 96, 96), (-1, -1, -1), (1, 1, 1)),       # 2n = 192 = 8 x 8 x 3
     ((128, 128, 128), (-1, -1, -1), (1, 1, 1)),    # 128^3 workload
+    ((10, 14, 20), (-1, -1, -1), (1, 1, 1)),       # 2n = 20, 28, 40: radix-5 and radix-7 stages
+    ((35, 25, 40), (-1, -1, -1.5), (1, 1.5, 1)),   # 2n = 70 = 2 x 5 x 7, 50 = 2 x 5 x 5, 80
+    ((80, 80, 80), (-1, -1, -1), (1, 1, 1)),       # 2n = 160 = 8 x 4 x 5
+    ((112, 70, 98), (-1, -1, -1), (1, 1, 1)),      # 2n = 224 = 8 x 4 x 7, 140, 196 = 4 x 7 x 7
 ]
 
 

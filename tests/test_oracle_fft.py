@@ -7,7 +7,8 @@ is known in closed form.
 import numpy as np
 import pytest
 
-LENGTHS = [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 18, 24, 27, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024]
+LENGTHS = [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 18, 20, 24, 25, 27, 28, 32, 35, 40, 48, 49, 64, 70, 96,
+           128, 140, 160, 192, 224, 256, 384, 512, 1024]
 
 
 def brute_dft(x, sign):
@@ -30,7 +31,7 @@ def test_fft_vs_brute_force_and_numpy(oracle, m, sign):
         assert np.abs(X - brute_dft(x, sign)).max() <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("m", [6, 64, 192, 1024])
+@pytest.mark.parametrize("m", [6, 64, 70, 192, 224, 1024])
 def test_fft_single_mode_closed_form(oracle, m):
     # x_j = exp(+2 pi i j k0 / m)  =>  forward DFT = m at k0, 0 elsewhere
     for k0 in [0, 1, m // 3, m - 1]:
