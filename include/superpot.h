@@ -156,8 +156,8 @@ sp_status sp_plan_copy_tables(sp_plan plan, double* gs_w, double* gs_a, double* 
  * sp_forward_spectrum -- diagnostic: only the forward half of Alg. 2.  Writes the
  * unnormalised padded DFT of rho, spec[kx][ky][kz] for kx < 2n0, ky < 2n1, kz <= n2,
  * as interleaved complex values of the pass type: float64 pairs (SP_FP64), float32 pairs
- * (SP_FP32, SP_MIXED), or double-float pairs (SP_DF32: re.hi, re.lo, im.hi, im.lo as
- * float32).  `spec` is device memory of 2n0 * 2n1 * (n2+1) complex values.  Uses the
+ * (SP_FP32, SP_MIXED), or double-float values (SP_DF32: four float32 per value, in the
+ * order re.hi, im.hi, re.lo, im.lo; re = re.hi + re.lo, im = im.hi + im.lo).  `spec` is device memory of 2n0 * 2n1 * (n2+1) complex values.  Uses the
  * plan's workspace.
  */
 sp_status sp_forward_spectrum(sp_plan plan, const void* rho, void* spec, sp_stream stream);

@@ -14,6 +14,9 @@ struct __align__(2 * sizeof(R)) cpx {
 };
 
 template <class R> SP_HD cpx<R> mk(R a, R b) { cpx<R> c; c.re = a; c.im = b; return c; }
+// Real and imaginary parts as values (a complex type may store its parts split).
+template <class R> SP_HD R re_of(cpx<R> c) { return c.re; }
+template <class R> SP_HD R im_of(cpx<R> c) { return c.im; }
 template <class R> SP_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk(a.re + b.re, a.im + b.im); }
 template <class R> SP_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk(a.re - b.re, a.im - b.im); }
 template <class R> SP_HD cpx<R> scale(cpx<R> a, R s) { return mk(a.re * s, a.im * s); }

@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include "sp_common.cuh"
+
 struct __align__(8) df32 {
     float hi, lo;
 };
@@ -118,4 +120,112 @@ __device__ __forceinline__ df32 df_norm(df32 a)
     df32 r;
     fast_two_sum(a.hi, a.lo, r.hi, r.lo);
     return r;
+}
+
+// ---------------------------------------------------------------------------------
+// Complex double-float values, stored and computed as pairs.  A complex value keeps
+// its high parts (re.hi, im.hi) and its low parts (re.lo, im.lo) side by side, so that
+// the real and imaginary halves of an addition run as one packed f32x2 instruction
+// (add/sub/fma.rn.f32x2: two independent IEEE round-to-nearest FP32 operations).  Each
+// lane computes exactly what the scalar double-float operation above computes, so the
+// results are bitwise those of the scalar form, in half the instructions.
+// Memory layout (16 bytes): re.hi, im.hi, re.lo, im.lo.
+// ---------------------------------------------------------------------------------
+template <> struct __align__(16) cpx<df32> {
+    float rh, ih, rl, il;
+};
+
+SP_HD cpx<df32> mk(df32 re, df32 im)
+{
+    cpx<df32> c;
+    c.rh = re.hi;
+    c.ih = im.hi;
+    c.rl = re.lo;
+    c.il = im.lo;
+    return c;
+}
+SP_HD df32 re_of(cpx<df32> c) { return df_make(c.rh, c.rl); }
+SP_HD df32 im_of(cpx<df32> c) { return df_make(c.ih, c.il); }
+
+typedef unsigned long long f32x2;  // two floats: first in the low 32 bits
+
+__device__ __forceinline__ f32x2 f2_pack(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 hi2(cpx<df32> c) { return f2_pack(c.rh, c.ih); }
+__device__ __forceinline__ f32x2 lo2(cpx<df32> c) { return f2_pack(c.rl, c.il); }
+__device__ __forceinline__ cpx<df32> from2(f32x2 h, f32x2 l)
+{
+    cpx<df32> c;
+    f2_unpack(h, c.rh, c.ih);
+    f2_unpack(l, c.rl, c.il);
+    return c;
+}
+
+// a + b: the double-float sum of each part (two-sum of the high parts, plus the sum of
+// the low parts), both parts at once.
+__device__ __forceinline__ cpx<df32> operator+(cpx<df32> a, cpx<df32> b)
+{
+    const f32x2 ah = hi2(a), bh = hi2(b);
+    const f32x2 s = f2_add(ah, bh);
+    const f32x2 bb = f2_sub(s, ah);
+    const f32x2 e = f2_add(f2_sub(ah, f2_sub(s, bb)), f2_sub(bh, bb));
+    return from2(s, f2_add(e, f2_add(lo2(a), lo2(b))));
+}
+
+// a - b, the two-sum of a.hi and -b.hi written with subtractions (negation is exact).
+__device__ __forceinline__ cpx<df32> operator-(cpx<df32> a, cpx<df32> b)
+{
+    const f32x2 ah = hi2(a), bh = hi2(b);
+    const f32x2 s = f2_sub(ah, bh);
+    const f32x2 bb = f2_sub(s, ah);
+    const f32x2 e = f2_sub(f2_sub(ah, f2_sub(s, bb)), f2_add(bh, bb));
+    return from2(s, f2_add(e, f2_sub(lo2(a), lo2(b))));
+}
+
+__device__ __forceinline__ cpx<df32> scale(cpx<df32> a, df32 s) { return mk(re_of(a) * s, im_of(a) * s); }
+SP_HD cpx<df32> conjg(cpx<df32> a)
+{
+    cpx<df32> c = a;
+    c.ih = -a.ih;
+    c.il = -a.il;
+    return c;
+}
+// a * (S i)
+template <int S> __device__ __forceinline__ cpx<df32> mul_si(cpx<df32> a)
+{
+    cpx<df32> c;
+    c.rh = S > 0 ? -a.ih : a.ih;
+    c.rl = S > 0 ? -a.il : a.il;
+    c.ih = S > 0 ? a.rh : -a.rh;
+    c.il = S > 0 ? a.rl : -a.rl;
+    return c;
+}
+
+// Renormalise both parts (fast two-sum of hi and lo).
+__device__ __forceinline__ cpx<df32> df_norm_c(cpx<df32> a)
+{
+    const f32x2 h = hi2(a), l = lo2(a);
+    const f32x2 s = f2_add(h, l);
+    return from2(s, f2_sub(l, f2_sub(s, h)));
 }

@@ -38,16 +38,18 @@ template <class R> SP_D cpx<R> tw_mul(cpx<R> a, cpx<R> w) { return cmul(a, w); }
 template <class R> SP_D cpx<R> tw_mulc(cpx<R> a, cpx<R> w) { return cmulc(a, w); }
 template <> SP_D cpx<df32> tw_mul<df32>(cpx<df32> a, cpx<df32> w)
 {
-    return mk(df_dot_sub(a.re, w.re, a.im, w.im), df_dot_add(a.re, w.im, a.im, w.re));
+    const df32 ar = re_of(a), ai = im_of(a), wr = re_of(w), wi = im_of(w);
+    return mk(df_dot_sub(ar, wr, ai, wi), df_dot_add(ar, wi, ai, wr));
 }
 template <> SP_D cpx<df32> tw_mulc<df32>(cpx<df32> a, cpx<df32> w)
 {
-    return mk(df_dot_add(a.re, w.re, a.im, w.im), df_dot_sub(a.im, w.re, a.re, w.im));
+    const df32 ar = re_of(a), ai = im_of(a), wr = re_of(w), wi = im_of(w);
+    return mk(df_dot_add(ar, wr, ai, wi), df_dot_sub(ai, wr, ar, wi));
 }
 
 // Values leaving registers (shared or global memory) are kept normalised.
 template <class R> SP_D cpx<R> norm(cpx<R> a) { return a; }
-template <> SP_D cpx<df32> norm<df32>(cpx<df32> a) { return mk(df_norm(a.re), df_norm(a.im)); }
+template <> SP_D cpx<df32> norm<df32>(cpx<df32> a) { return df_norm_c(a); }
 
 // ------------------------------------------------------------------ plans
 // Forward radices: powers of two first (the first stage is radix 8, so zero padding

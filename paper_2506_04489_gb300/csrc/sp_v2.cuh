@@ -373,12 +373,12 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int z = first_element<N, false>(t, j);
-        cpx<R> x = czero<R>();
+        R xr = Num<R>::c(0.0), xi = Num<R>::c(0.0);
         if ((j % R0) < R0 / 2) {  // z < n2: the padded half is zero
-            if (l0 < a.lines) x.re = to_r<R, Tio>(rho[l0 * n2 + z]);
-            if (l1 < a.lines) x.im = to_r<R, Tio>(rho[l1 * n2 + z]);
+            if (l0 < a.lines) xr = to_r<R, Tio>(rho[l0 * n2 + z]);
+            if (l1 < a.lines) xi = to_r<R, Tio>(rho[l1 * n2 + z]);
         }
-        v[j] = x;
+        v[j] = mk(xr, xi);
     }
     __syncthreads();
     cpx<R>* sm = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
         const cpx<R> zm = conjg(sm[lay(k == 0 ? 0 : N - k)]);
         const cpx<R> s = zk + zm, d = zk - zm;
         if (l0 < a.lines) W[r0 + k] = norm(half_of(s));
-        if (l1 < a.lines) W[r1 + k] = norm(half_of(mk(d.im, -d.re)));
+        if (l1 < a.lines) W[r1 + k] = norm(half_of(mk(im_of(d), -re_of(d))));
     }
 }
 
@@ -418,14 +418,13 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     // Z_k = Xa_k + i Xb_k from the Hermitian halves (DC and Nyquist take real parts)
     const long long r0 = w_row(a, l0), r1 = w_row(a, l1 < a.lines ? l1 : l0);
     for (int k = t; k <= n2; k += T) {
-        cpx<R> xa = l0 < a.lines ? W[r0 + k] : czero<R>();
-        cpx<R> xb = l1 < a.lines ? W[r1 + k] : czero<R>();
-        if (k == 0 || k == n2) {
-            xa.im = Num<R>::c(0.0);
-            xb.im = Num<R>::c(0.0);
-        }
-        sm0[lay(k)] = norm(mk(xa.re - xb.im, xa.im + xb.re));
-        if (k > 0 && k < n2) sm0[lay(N - k)] = norm(mk(xa.re + xb.im, xb.re - xa.im));
+        const cpx<R> xa = l0 < a.lines ? W[r0 + k] : czero<R>();
+        const cpx<R> xb = l1 < a.lines ? W[r1 + k] : czero<R>();
+        const R ar = re_of(xa), br = re_of(xb);
+        const bool edge = k == 0 || k == n2;
+        const R ai = edge ? Num<R>::c(0.0) : im_of(xa), bi = edge ? Num<R>::c(0.0) : im_of(xb);
+        sm0[lay(k)] = norm(mk(ar - bi, ai + br));
+        if (k > 0 && k < n2) sm0[lay(N - k)] = norm(mk(ar + bi, br - ai));
     }
     __syncthreads();
     cpx<R> v[E];
@@ -436,8 +435,8 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     for (int j = 0; j < E; ++j) {
         if ((j % R0) < R0 / 2) {  // z < n2
             const int z = last_element<N, true>(t, j);
-            if (l0 < a.lines) u[l0 * n2 + z] = from_r<R, Tio>(v[j].re);
-            if (l1 < a.lines) u[l1 * n2 + z] = from_r<R, Tio>(v[j].im);
+            if (l0 < a.lines) u[l0 * n2 + z] = from_r<R, Tio>(re_of(v[j]));
+            if (l1 < a.lines) u[l1 * n2 + z] = from_r<R, Tio>(im_of(v[j]));
         }
     }
 }

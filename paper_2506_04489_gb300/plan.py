@@ -247,7 +247,7 @@ class Plan:
         import torch
         self._check_io(rho, False)
         shape = (2 * self.n[0], 2 * self.n[1], self.n[2] + 1)
-        if self.precision == "df32":  # (re.hi, re.lo, im.hi, im.lo) float32 per value
+        if self.precision == "df32":  # (re.hi, im.hi, re.lo, im.lo) float32 per value
             spec = torch.empty(shape + (4,), dtype=torch.float32, device=rho.device)
         else:
             cdt = torch.complex128 if self.precision == "fp64" else torch.complex64

@@ -42,9 +42,9 @@ def test_sampled_spectrum_coefficients(oracle, n, precision):
     for k in ks:
         ref = oracle.dft_coeff(rho, k)
         s = spec[k]
-        if precision == "df32":  # (re.hi, re.lo, im.hi, im.lo)
+        if precision == "df32":  # (re.hi, im.hi, re.lo, im.lo)
             s = s.double().cpu().numpy()
-            got = complex(s[0] + s[1], s[2] + s[3])
+            got = complex(s[0] + s[2], s[1] + s[3])
         else:
             got = complex(s.item())
         assert abs(got - ref) <= 1e-13 * scale, (k, got, ref)
