@@ -55,7 +55,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 // Sum without a final renormalisation: hi + lo carries the sum with an error of at
 // most a few 2^-48 (|a| + |b|); lo may exceed ulp(hi)/2 by a small factor, which the
 // exact two-sum of the high parts and the cross terms of the product absorb.  Values
-// are renormalised (df_norm) only where they leave registers.
+// are renormalised (df_norm) only where they are written to global memory.
 __device__ __forceinline__ df32 operator+(df32 a, df32 b)
 {
     float s, e;
@@ -229,3 +229,15 @@ __device__ __forceinline__ cpx<df32> df_norm_c(cpx<df32> a)
     const f32x2 s = f2_add(h, l);
     return from2(s, f2_sub(l, f2_sub(s, h)));
 }
+
+// Single-precision complex sums as one packed instruction: cpx<float> keeps re, im side
+// by side (8 bytes), exactly an f32x2 pair; each lane rounds as the scalar sum would.
+__device__ __forceinline__ f32x2 as_f2(cpx<float> a) { return f2_pack(a.re, a.im); }
+__device__ __forceinline__ cpx<float> from_f2(f32x2 v)
+{
+    cpx<float> c;
+    f2_unpack(v, c.re, c.im);
+    return c;
+}
+__device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) { return from_f2(f2_add(as_f2(a), as_f2(b))); }
+__device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) { return from_f2(f2_sub(as_f2(a), as_f2(b))); }

@@ -47,7 +47,10 @@ template <> SP_D cpx<df32> tw_mulc<df32>(cpx<df32> a, cpx<df32> w)
     return mk(df_dot_add(ar, wr, ai, wi), df_dot_sub(ai, wr, ar, wi));
 }
 
-// Values leaving registers (shared or global memory) are kept normalised.
+// Values written to global memory are renormalised.  Exchanges through shared memory
+// between the stages of one transform keep the pair as the arithmetic left it: sums and
+// products accept a low part of a few ulps of the high part (their error stays a small
+// multiple of 2^-48 of the operands), so renormalising there would only cost FP32 work.
 template <class R> SP_D cpx<R> norm(cpx<R> a) { return a; }
 template <> SP_D cpx<df32> norm<df32>(cpx<df32> a) { return df_norm_c(a); }
 
@@ -241,15 +244,15 @@ template <class R, int N, bool INV, int ST> struct Stage {
                 cpx<R>* p0 = sm + lay(base);
                 const int st = lay.step(P);
 #pragma unroll
-                for (int q = 0; q < RAD; ++q) p0[q * st] = norm(v[m * RAD + q]);
+                for (int q = 0; q < RAD; ++q) p0[q * st] = v[m * RAD + q];
             } else if constexpr (P == 1 && RAD == 8) {
                 cpx<R>* p0 = sm + lay(base);  // base = 8 i
                 const int st = lay.unit();
 #pragma unroll
-                for (int q = 0; q < RAD; ++q) p0[q * st] = norm(v[m * RAD + q]);
+                for (int q = 0; q < RAD; ++q) p0[q * st] = v[m * RAD + q];
             } else {
 #pragma unroll
-                for (int q = 0; q < RAD; ++q) sm[lay(base + q * P)] = norm(v[m * RAD + q]);
+                for (int q = 0; q < RAD; ++q) sm[lay(base + q * P)] = v[m * RAD + q];
             }
         }
     }

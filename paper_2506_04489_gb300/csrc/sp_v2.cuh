@@ -383,7 +383,7 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     __syncthreads();
     cpx<R>* sm = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
 #pragma unroll
-    for (int j = 0; j < E; ++j) sm[lay(last_element<N, false>(t, j))] = norm(v[j]);
+    for (int j = 0; j < E; ++j) sm[lay(last_element<N, false>(t, j))] = v[j];
     __syncthreads();
     // two real lines from one complex transform: Xa = (Z_k + conj Z_{N-k}) / 2,
     // Xb = (Z_k - conj Z_{N-k}) / (2 i), k = 0..n2
@@ -423,8 +423,8 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
         const R ar = re_of(xa), br = re_of(xb);
         const bool edge = k == 0 || k == n2;
         const R ai = edge ? Num<R>::c(0.0) : im_of(xa), bi = edge ? Num<R>::c(0.0) : im_of(xb);
-        sm0[lay(k)] = norm(mk(ar - bi, ai + br));
-        if (k > 0 && k < n2) sm0[lay(N - k)] = norm(mk(ar + bi, br - ai));
+        sm0[lay(k)] = mk(ar - bi, ai + br);
+        if (k > 0 && k < n2) sm0[lay(N - k)] = mk(ar + bi, br - ai);
     }
     __syncthreads();
     cpx<R> v[E];
