@@ -3,8 +3,10 @@
 
 Metric: grid points per second (output points n^3 per second) of the solve phase
 (Alg. 2; the one-time precompute of Alg. 1 is excluded, as in the paper's timings) on
-the 256^3 workload: the C-infinity bump density exp(-1/(1 - r^2/0.64)) on [-1,1]^3,
-FP64 (value) with the FP32 path reported beside it.
+the 256^3 workload: the C-infinity bump density exp(-1/(1 - r^2/0.64)) on [-1,1]^3.
+The value is the FP64-accuracy path (FP64 in and out, double-float passes on the FP32
+pipes, within 1e-12 of the FP64 oracle); native FP64 passes and the FP32 path are
+reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,6 +52,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     ap.add_argument("--profile", nargs=3, metavar=("N", "PRECISION", "SOLVES"),
                     help="only build one plan and run SOLVES solves (a small target for ncu)")
+    ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV",
+                    help="write profiles/ncu_counts.txt from ncu launch lists launches_<n>_<prec>.csv")
     return ap.parse_args()
 
 
@@ -108,20 +112,92 @@ def source_hash():
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+COUNTS_FILE = os.path.join(ROOT, "profiles", "ncu_counts.txt")
+PASS_OF_KERNEL = (("k2_z_fwd", "z_forward"), ("k2_z_inv", "z_inverse"), ("k3_line<", None), ("k2_line<", None))
+LINE_MODES = {"0": "y_forward", "1": "y_inverse", "2": "x_multiply"}
+
+
+def ncu_count(kernel, workload, metric):
+    """Per-launch count `metric` of pass `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
     try:
         cur = source_hash()
-        with open(path) as f:
+        with open(COUNTS_FILE) as f:
             for line in f:
                 t = line.split()
-                if len(t) == 4 and not line.startswith("#") and t[0] == kernel and t[1] == workload and t[3] == cur:
-                    return float(t[2])
+                if (len(t) == 5 and not line.startswith("#") and t[0] == kernel and t[1] == workload
+                        and t[2] == metric and t[4] == cur):
+                    return float(t[3])
     except OSError:
         pass
     return None
+
+
+def _pass_name(kernel_name, seen):
+    """Solve pass of an ncu kernel name (line passes carry their mode as the third
+    template argument; y passes come before and after the x pass in launch order)."""
+    for prefix, name in PASS_OF_KERNEL:
+        if kernel_name.startswith("void " + prefix) or kernel_name.startswith(prefix):
+            if name:
+                return name
+            mode = kernel_name.split("<", 1)[1].split(",")[2].strip().rstrip(">").split(">")[0]
+            return LINE_MODES.get(mode)
+    return None
+
+
+def ingest_ncu(paths):
+    """Turn ncu launch lists (--csv, one file per workload, named launches_<n>_<prec>.csv;
+    metrics gpu__time_duration, dram bytes and the FP32 instruction counts) into the
+    per-launch counts that bench.py reads, tagged with the current source hash, and print
+    a markdown table per workload."""
+    import collections
+    import csv
+    cur = source_hash()
+    keep = []
+    try:
+        with open(COUNTS_FILE) as f:
+            keep = [ln for ln in f if not ln.startswith("#") and ln.split() and ln.split()[-1] == cur]
+    except OSError:
+        pass
+    rows_out = {}
+    for path in paths:
+        base = os.path.basename(path)[:-4].split("_")  # launches, n, prec
+        workload = f"n{base[1]}_{base[2]}"
+        launches = collections.OrderedDict()
+        with open(path) as f:
+            for r in csv.DictReader(ln for ln in f if not ln.startswith("==")):
+                launches.setdefault(r["ID"], {"kernel": r["Kernel Name"]})[r["Metric Name"]] = float(
+                    r["Metric Value"].replace(",", ""))
+        agg = collections.OrderedDict()
+        for m in launches.values():
+            name = _pass_name(m["kernel"], agg)
+            if name is None:
+                continue
+            a = agg.setdefault(name, {"kernel": m["kernel"], "n": 0, "time_ns": 0.0, "dram": 0.0, "fp32_ops": 0.0})
+            a["n"] += 1
+            a["time_ns"] += m.get("gpu__time_duration.sum", 0.0)
+            a["dram"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+            one = sum(m.get(f"smsp__sass_thread_inst_executed_op_{op}_pred_on.sum", 0.0) for op in ("fadd", "fmul", "ffma"))
+            two = sum(m.get(f"smsp__sass_thread_inst_executed_op_{op}2_pred_on.sum", 0.0) for op in ("fadd", "fmul", "ffma"))
+            a["fp32_ops"] += one + 2.0 * two
+        tot = sum(a["time_ns"] for a in agg.values()) or 1.0
+        print(f"\n## {workload}\n\n| pass | kernel | launches | avg ms | share | DRAM MB/launch | FP32 lane-ops/launch |")
+        print("|---|---|---|---|---|---|---|")
+        for name, a in agg.items():
+            k = a["n"]
+            print(f"| {name} | {a['kernel'].replace('void ', '').rsplit('(', 1)[0]} | {k} | {a['time_ns'] / k / 1e6:.3f} | "
+                  f"{a['time_ns'] / tot:.3f} | {a['dram'] / k / 1e6:.1f} | {a['fp32_ops'] / k:.4g} |")
+            rows_out[(name, workload, "dram_bytes")] = a["dram"] / k
+            if a["fp32_ops"] > 0:
+                rows_out[(name, workload, "fp32_lane_ops")] = a["fp32_ops"] / k
+    keep = [ln for ln in keep if tuple(ln.split()[:3]) not in rows_out]
+    with open(COUNTS_FILE, "w") as f:
+        f.write("# per-launch counts from ncu launch lists of the bench workload (python bench.py --ingest-ncu)\n"
+                "# pass workload metric value source-hash (bench.py uses a row only while the hash matches)\n")
+        f.writelines(keep)
+        for (name, workload, metric), v in rows_out.items():
+            f.write(f"{name} {workload} {metric} {v:.6g} {cur}\n")
+    return 0
 
 
 class ClockSampler:
@@ -267,6 +343,11 @@ def time_solves(plan, rhos, outs, steps, warmup, world, stream):
     return max_over_ranks(ms, world), plan.pass_times()
 
 
+# FP32 pipe of the chip: 152 SMs x 128 FP32 lanes, one operation per lane per clock
+# (an FMA counts once) at the 2070 MHz maximum SM clock
+FP32_LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
 def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
     model = pass_model(n, prec)
     name = max(passes, key=lambda k: passes[k][0])
@@ -274,29 +355,38 @@ def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
     avg_s = tot_ms / max(launches, 1) / 1e3
     nbytes, nflops = model[name]
     workload = f"n{n}_{prec}"
+    traffic = ncu_count(name, workload, "dram_bytes")
     if prec == "fp64":
         achieved = nflops / avg_s / 1e12
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); HBM view in hbm_roofline",
-                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
                 "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
     elif prec == "df32":
-        # FP64-class flops carried out in double-float on the FP32 pipes, counted as FP64
-        # flops of the same algorithm; HBM view of the same kernel beside it
-        achieved = nflops / avg_s / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "unit": "TFLOP/s (FP64-class)",
-                "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s): the rate native FP64 arithmetic "
-                               "would need; above 1 means the double-float path beats native FP64",
+        # double-float arithmetic runs on the FP32 pipe: the operations one launch executes
+        # (ncu instruction counts of this kernel on this workload, f32x2 forms twice) over
+        # its live average duration, against the pipe's one-per-lane-per-clock ceiling
+        ops = ncu_count(name, workload, "fp32_lane_ops")
+        achieved = ops / avg_s / 1e12 if ops else None
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "unit": "T FP32 lane-ops/s",
+                "peak": FP32_LANE_PEAK_TOPS, "frac": achieved / FP32_LANE_PEAK_TOPS if ops else None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts and maximum clock; an FMA "
+                               "counts once)",
+                "ops_per_launch": ops,
+                "ops_source": "ncu FP32 instruction counts (fadd, fmul, ffma; f32x2 forms twice) of this "
+                              "kernel on this workload, profiles/ncu_counts.txt" if ops else
+                              "not captured for the current kernel sources",
+                "fp64_class": {"achieved": nflops / avg_s / 1e12, "unit": "TFLOP/s (5 N log2 N convention)",
+                               "vs_nominal_fp64_peak": nflops / avg_s / 1e12 / FP64_PEAK_TFLOPS},
                 "hbm_gbs": nbytes / avg_s / 1e9, "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak,
-                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
                 "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
     else:
         achieved = nbytes / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": ncu_traffic(name, workload), "avg_launch_ms": avg_s * 1e3,
+                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
                 "algorithmic_bytes": nbytes}
     share = {k: round(v[0] / sum(x[0] for x in passes.values()), 4) for k, v in passes.items()}
     roof["pass_share"] = share
@@ -446,25 +536,33 @@ def run_ours(args, world, rank, local):
 
 
 def run_profile_case(args):
-    """One plan of grid N^3 and the given precision, then SOLVES solves of the bump
-    density: the launch sequence that the ncu summaries under profiles/ capture."""
+    """One plan of grid N^3 and the given precision, autotuned as in the bench, then
+    SOLVES solves of the bump density inside an NVTX range named "solves" (ncu
+    --nvtx --nvtx-include solves/ captures just those launches): the launch sequence
+    that the ncu summaries under profiles/ capture."""
     import torch
 
     from paper_2506_04489_gb300 import Plan, workloads as W
     n, prec, k = int(args.profile[0]), args.profile[1], int(args.profile[2])
     plan = Plan(n, BOX[0], BOX[1], precision=prec)
+    plan.autotune(1)
     rho = torch.from_numpy(W.bump_profile(n, *BOX)).cuda().to(plan.dtype)
     out = torch.empty_like(rho)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("solves")
     for _ in range(k):
         plan.solve(rho, out)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": {"n": n, "precision": prec, "solves": k}}))
+    print(json.dumps({"profile_case": {"n": n, "precision": prec, "solves": k, "tiles": plan.tiles()}}))
     plan.close()
     return 0
 
 
 def main():
     args = parse()
+    if args.ingest_ncu:
+        return ingest_ncu(args.ingest_ncu)
     if args.profile:
         return run_profile_case(args)
     if args.impl == "reference":
