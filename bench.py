@@ -423,6 +423,49 @@ def run_served(args):
     return summary
 
 
+def run_cufft_comparison(n, rho_np, m_octant, ref_u, steps, warmup, stream):
+    """The same padded convolution (Alg. 2) with torch.fft, i.e. cuFFT, in FP64 and in
+    FP32: pad into a zeroed (2n)^3 buffer, real-to-complex FFT, multiply by the plan's own
+    multiplier (expanded from its octant by evenness), complex-to-real FFT, crop.  A
+    comparison for the hand-written passes only; the library never calls it."""
+    import torch
+    N = 2 * n
+    k = torch.arange(N)
+    fold = torch.minimum(k, N - k)
+    m64 = torch.from_numpy(m_octant)  # [|kx|][|ky|][kz], already divided by Ntilde
+    out = {}
+    for prec, rdt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        mult = m64[fold][:, fold].to("cuda", dtype=rdt).contiguous()
+        pad = torch.zeros((N, N, N), dtype=rdt, device="cuda")
+        rho = torch.from_numpy(rho_np).to("cuda", dtype=rdt)
+        u = torch.empty_like(rho)
+
+        def solve():
+            pad[:n, :n, :n].copy_(rho)
+            spec = torch.fft.rfftn(pad)
+            spec.mul_(mult)
+            u.copy_(torch.fft.irfftn(spec, s=(N, N, N), norm="forward")[:n, :n, :n])
+
+        for _ in range(max(warmup, 3)):
+            solve()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(steps):
+            solve()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / steps
+        dev = float((u.double() - ref_u).abs().max() / ref_u.abs().max())
+        out[prec] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": "grid pts/s",
+                     "max_rel_dev_from_fp64": dev}
+        del mult, pad, rho, u
+        torch.cuda.empty_cache()
+    out["note"] = ("torch.fft (cuFFT) running the same padded convolution with the same multiplier: "
+                   "a comparison only, not the product path")
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -460,6 +503,7 @@ def run_ours(args, world, rank, local):
         if prec == "fp64":
             ref_u = u_dev.clone()
             rel_dev = 0.0
+            m_octant = plan.tables(0)["M"]  # multiplier / Ntilde, for the cuFFT comparison
         else:
             rel_dev = float((u_dev - ref_u).abs().max() / ref_u.abs().max())
         results[prec] = {"value": value, "ms_per_step": ms_step, "roofline": roof,
@@ -471,12 +515,12 @@ def run_ours(args, world, rank, local):
         # end to end through the public API: pinned host densities -> device -> solve ->
         # pinned host potentials, each step's copies overlapped with its neighbours' solves
         if prec == "df32":
-            e2e_steps = max(3, args.steps // 2)
+            e2e_steps = max(10, args.steps)
             host_in = [torch.from_numpy(rho_np).to(dtype=dt).pin_memory() for _ in range(2)]
             host_out = [torch.empty(host_in[0].shape, dtype=dt, pin_memory=True) for _ in range(2)]
             ins = [host_in[i % 2] for i in range(e2e_steps)]
             outs_h = [host_out[i % 2] for i in range(e2e_steps)]
-            plan.solve_host_stream(ins[:2], outs_h[:2], stream)  # warm-up
+            plan.solve_host_stream(ins[:4], outs_h[:4], stream)  # warm-up (streams, staging buffers)
             torch.cuda.synchronize()
             barrier(world)
             t0 = time.perf_counter()
@@ -492,6 +536,9 @@ def run_ours(args, world, rank, local):
         plan.close()
         del rhos, outs, base
         torch.cuda.empty_cache()
+    cufft = run_cufft_comparison(n, rho_np, m_octant, ref_u, args.steps, args.warmup, stream)
+    del ref_u
+    torch.cuda.empty_cache()
     served = None
     if world == 1 and not args.no_serve:
         served = run_served(args)
@@ -525,6 +572,7 @@ def run_ours(args, world, rank, local):
                  "hbm_roofline": results["fp32"]["hbm_roofline"],
                  "max_rel_dev_from_fp64": results["fp32"]["max_rel_dev_from_fp64"]},
         "e2e": results["e2e"],
+        "cufft_comparison": cufft,
         "served": served,
         "gpu_launches": r64["gpu_launches"],
         "clocks": clocks,

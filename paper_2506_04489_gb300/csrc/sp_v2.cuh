@@ -243,17 +243,26 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
     if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws, twg, tid, blockDim.x);
     if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws, twg, tid, blockDim.x);
     const Lay lay(LGB, b);
-    auto decode = [&](int tile, int& batch, int& o, int& cb) {
-        cb = tile % pa.ncb;
-        const int r = tile / pa.ncb;
-        o = r % pa.outer;
-        batch = r / pa.outer;
-    };
-    auto issue = [&](int tile) {
+    // tile index = (batch * outer + o) * ncb + cb.  The first tile is decoded by division;
+    // each later one adds gridDim.x in that mixed radix (two compares, no division).
+    struct TileIdx {
         int batch, o, cb;
-        decode(tile, batch, o, cb);
-        const char* src = reinterpret_cast<const char*>(static_cast<const cpx<R>*>(a.in) + batch * a.in_bs +
-                                                        o * a.in_os + cb * B);
+    };
+    const int g_cb = (int)gridDim.x % pa.ncb, g_r = (int)gridDim.x / pa.ncb;
+    const int g_o = g_r % pa.outer, g_b = g_r / pa.outer;
+    auto advance = [&](TileIdx x) {
+        x.cb += g_cb;
+        int carry = x.cb >= pa.ncb;
+        if (carry) x.cb -= pa.ncb;
+        x.o += g_o + carry;
+        carry = x.o >= pa.outer;
+        if (carry) x.o -= pa.outer;
+        x.batch += g_b + carry;
+        return x;
+    };
+    auto issue = [&](TileIdx x) {
+        const char* src = reinterpret_cast<const char*>(static_cast<const cpx<R>*>(a.in) + x.batch * a.in_bs +
+                                                        x.o * a.in_os + x.cb * B);
         for (int q = tid; q < NIN * CH; q += blockDim.x) {
             const int row = q / CH, ch = q % CH;
             cp_async16(reinterpret_cast<char*>(stg) + (size_t)row * B * sizeof(cpx<R>) + ch * 16,
@@ -261,10 +270,14 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
         }
         cp_async_commit();
     };
-    if (blockIdx.x < pa.ntiles) issue(blockIdx.x);
+    TileIdx cur;
+    cur.cb = (int)blockIdx.x % pa.ncb;
+    cur.o = ((int)blockIdx.x / pa.ncb) % pa.outer;
+    cur.batch = ((int)blockIdx.x / pa.ncb) / pa.outer;
+    if (blockIdx.x < pa.ntiles) issue(cur);
     for (int tile = blockIdx.x; tile < pa.ntiles; tile += gridDim.x) {
-        int batch, o, cb;
-        decode(tile, batch, o, cb);
+        const TileIdx nxt = advance(cur);
+        const int batch = cur.batch, o = cur.o, cb = cur.cb;
         const int c = cb * B + b;
         const bool cv = c < a.ncol;
         cp_async_wait_all();
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
             }
         }
         __syncthreads();  // the stage is free: start the next tile's copies
-        if (tile + (int)gridDim.x < pa.ntiles) issue(tile + gridDim.x);
+        if (tile + (int)gridDim.x < pa.ntiles) issue(nxt);
         cpx<R>* fresh;
         if constexpr (MODE == INV) {
             fresh = run_stages<R, N, true, +1, false>(v, sm0, sm1, lay, tws, t);
@@ -322,6 +335,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
                 if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
         }
         __syncthreads();  // exchange buffers free before the next tile's first write
+        cur = nxt;
     }
     cp_async_wait_all();
 }
