@@ -208,12 +208,21 @@ struct PArgs {
 };
 
 template <class R, int N, int MODE> constexpr int stage_rows() { return MODE == INV ? N : N / 2; }
+// Two exchange buffers when they fit beside the twiddles and the stage in 110 KB (two CTAs
+// per SM), else one.
+template <class R, int N, int MODE> constexpr bool pipe_two_buffers()
+{
+    constexpr int B = 1 << lg_default<N>();
+    constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
+    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
+    return twb + 2 * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B <= 110 * 1024;
+}
 template <class R, int N, int MODE> constexpr size_t pipe_smem()
 {
     constexpr int B = 1 << lg_default<N>();
     constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
     constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
-    return twb + (two_buffers(buf, twb) ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
+    return twb + (pipe_two_buffers<R, N, MODE>() ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
 }
 
 template <class R, int N, int MODE>
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
     static_assert((B * sizeof(cpx<R>)) % 16 == 0, "stage row alignment");
     const LArgs& a = pa.a;
     const int BUF = Lay::size(N, B);
-    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, sizeof(cpx<R>) * tw_entries<R, N>());
+    constexpr bool DB = pipe_two_buffers<R, N, MODE>();
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws + tw_entries<R, N>();
