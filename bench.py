@@ -400,7 +400,8 @@ def run_served(args):
     """Served stream: Poisson arrivals (mean 200/s, seed 0) of solves with n drawn from
     {32, 64, 96, 128, 192, 256} and accuracy from {1e-6 (FP32), 1e-12 (double-float)}, bump
     densities, device-resident plans (built before traffic) under a 120 GB budget; p50/p99
-    latency and solves/s over the requests arriving after a 2 s warm-up."""
+    latency and solves/s over the requests arriving after a 2 s warm-up; results go to
+    pinned buffers the client owns and reuses."""
     import torch
 
     from paper_2506_04489_gb300 import serve, workloads as W
@@ -412,11 +413,13 @@ def run_served(args):
             dens[(n, prec)] = torch.from_numpy(b).to(dt).pin_memory()
     srv = serve.Server(BOX[0], BOX[1], budget_bytes=120e9, max_batch=8, slots=4)
     srv.prepare(dens.keys())  # resident plans for every key before traffic starts
+    # the client's own result buffers (pinned), reused as results are consumed
+    outputs = {k: [v.new_empty(v.shape).pin_memory() for _ in range(4)] for k, v in dens.items()}
     srv.start()
     warm = 2.0
     t0 = time.monotonic()
     serve.poisson_stream(srv, rate=200.0, duration=args.serve_seconds, sizes=sizes, accuracies=(1e-6, 1e-12),
-                         seed=0, densities=dens, warmup=warm)
+                         seed=0, densities=dens, warmup=warm, outputs=outputs)
     summary = serve.latency_summary(srv, t0 + warm, t0 + warm + args.serve_seconds)
     srv.stop()
     if summary is not None:

@@ -50,20 +50,22 @@ def entry_bytes(n: int, precision: str, max_batch: int) -> int:
     return work + tables + io + (1 << 20)
 
 
-Done = collections.namedtuple("Done", "arrival done_at key")
+Done = collections.namedtuple("Done", "arrival done_at key launched_at", defaults=(None,))
 
 
 class Request:
-    __slots__ = ("rho", "accuracy", "n", "precision", "arrival", "future", "done_at")
+    __slots__ = ("rho", "out", "accuracy", "n", "precision", "arrival", "future", "done_at", "launched_at")
 
-    def __init__(self, rho, accuracy, arrival):
+    def __init__(self, rho, accuracy, arrival, out=None):
         self.rho = rho
+        self.out = out
         self.accuracy = accuracy
         self.n = int(rho.shape[0])
         self.precision = precision_for(accuracy)
         self.arrival = arrival
         self.future = Future()
         self.done_at = None
+        self.launched_at = None
 
 
 class _Entry:
@@ -85,6 +87,15 @@ def batch_cap(n: int, max_batch: int, max_points: int) -> int:
     return max(1, min(int(max_batch), int(max_points) // n ** 3))
 
 
+def pick_slot(free, priority_slots: int, small: bool) -> int:
+    """Free slot for a batch: slots [0, priority_slots) are high-priority streams, taken
+    first by small batches and last by large ones."""
+    hi = [i for i in free if i < priority_slots]
+    lo = [i for i in free if i >= priority_slots]
+    order = hi + lo if small else lo + hi
+    return order[0]
+
+
 class Server:
     """Continuous-batching server for solves on the box [lo, hi]^3.
 
@@ -94,13 +105,18 @@ class Server:
                     large grids is cut at this size so a request queued behind it waits for
                     a bounded amount of work, not for max_batch full-size solves.
     slots         : concurrent batches (CUDA streams).
+    priority_slots: how many of the slots run on high-priority streams.  Batches of at
+                    most small_points grid points go to those first, so the block
+                    scheduler runs their kernels' blocks ahead of a large solve's
+                    waiting blocks instead of queueing them behind whole passes.
     plans_per_key : resident plans per (n, precision); further requests of a busy key wait
                     and are batched together when a plan frees up.
     """
 
     def __init__(self, lo: float = -1.0, hi: float = 1.0, budget_bytes: float = 120e9, max_batch: int = 8,
-                 slots: int = 4, device: int = 0, plans_per_key: int = 2,
-                 max_batch_points: int = 2 * 256 ** 3):
+                 slots: int = 4, device: int = 0, plans_per_key: int = 2, priority_slots: int = 2,
+                 small_points: int = 2 * 128 ** 3,
+                 max_batch_points: int = 256 ** 3):
         import torch
         self.torch = torch
         self.plans_per_key = int(plans_per_key)
@@ -109,7 +125,11 @@ class Server:
         self.max_batch = int(max_batch)
         self.max_batch_points = int(max_batch_points)
         self.device = torch.device("cuda", device)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        hi_prio = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
+        self.priority_slots = max(0, min(int(priority_slots), slots - 1))
+        self.small_points = int(small_points)
+        self.streams = [torch.cuda.Stream(device=self.device, priority=hi_prio if i < self.priority_slots else 0)
+                        for i in range(slots)]
         self.slot_busy = [None] * slots  # (event, entry, [(request, host_out)])
         self.pending = collections.OrderedDict()  # key -> deque of requests
         self.entries = {}  # key -> [_Entry]
@@ -128,11 +148,13 @@ class Server:
         self._thread.start()
         return self
 
-    def submit(self, rho, accuracy: float, arrival: float = None) -> Future:
+    def submit(self, rho, accuracy: float, arrival: float = None, out=None) -> Future:
         """Queue one solve.  rho: a CPU torch tensor (pinned for asynchronous copies) of
         shape (n, n, n), float32 for accuracy >= 1e-6 else float64.  The future yields
-        the potential as a CPU tensor of the same shape and type."""
-        req = Request(rho, accuracy, time.monotonic() if arrival is None else arrival)
+        the potential as a CPU tensor of the same shape and type: `out` if given (a
+        pinned CPU tensor like rho, which the caller must not touch until the future is
+        done), else a new pinned tensor."""
+        req = Request(rho, accuracy, time.monotonic() if arrival is None else arrival, out)
         with self._lock:
             self.pending.setdefault((req.n, req.precision), collections.deque()).append(req)
         self._wake.set()
@@ -218,7 +240,7 @@ class Server:
                     req.done_at = t
                     # only (arrival, completion, key) is kept: results belong to the client,
                     # so their pinned buffers return to the allocator's cache once dropped
-                    self.completed.append(Done(req.arrival, t, (req.n, req.precision)))
+                    self.completed.append(Done(req.arrival, t, (req.n, req.precision), req.launched_at))
                     req.future.set_result(host_out)
                 entry.busy = False
                 entry.last_used = t
@@ -237,17 +259,24 @@ class Server:
                 r.future.set_exception(ValueError(
                     f"request needs a CPU {dtype} tensor of shape {(entry.key[0],) * 3}"))
                 continue
+            if r.out is not None and (tuple(r.out.shape) != tuple(r.rho.shape) or r.out.dtype != dtype
+                                      or r.out.is_cuda or not r.out.is_contiguous()):
+                r.future.set_exception(ValueError(f"out must be a contiguous CPU {dtype} tensor like rho"))
+                continue
             good.append(r)
         if not good:
             entry.busy = False
             return
         b = len(good)
+        t_launch = time.monotonic()
+        for r in good:
+            r.launched_at = t_launch
         with torch.cuda.stream(st):
             for i, r in enumerate(good):
                 entry.in_buf[i].copy_(r.rho, non_blocking=True)
             entry.plan.solve_batched(entry.in_buf[:b], entry.out_buf[:b], st)
             for i, r in enumerate(good):
-                host = torch.empty(r.rho.shape, dtype=dtype, pin_memory=True)
+                host = r.out if r.out is not None else torch.empty(r.rho.shape, dtype=dtype, pin_memory=True)
                 host.copy_(entry.out_buf[i], non_blocking=True)
                 items.append((r, host))
             ev = torch.cuda.Event()
@@ -281,7 +310,8 @@ class Server:
                     cap = batch_cap(key[0], self.max_batch, self.max_batch_points)
                     reqs = [q.popleft() for _ in range(min(cap, len(q)))]
                 entry.busy = True
-                self._launch(free[0], entry, reqs)
+                self._launch(pick_slot(free, self.priority_slots, len(reqs) * key[0] ** 3 <= self.small_points),
+                             entry, reqs)
                 launched = started = True
                 break
             if not started:
@@ -307,11 +337,14 @@ class Server:
 
 
 def poisson_stream(server: Server, rate: float, duration: float, sizes, accuracies, seed: int = 0,
-                   densities=None, warmup: float = 0.0):
+                   densities=None, warmup: float = 0.0, outputs=None):
     """Drive `server` with Poisson arrivals (mean `rate` per second) for `warmup + duration`
     seconds; each request draws its grid size and accuracy uniformly from the lists.
-    `densities[(n, precision)]` supplies the (pinned CPU) input of a key.  Returns the
-    requests that arrived after the warm-up, completed."""
+    `densities[(n, precision)]` supplies the (pinned CPU) input of a key.  With `outputs`
+    (key -> list of pinned CPU tensors like the density), results land in buffers taken
+    from that pool and returned to it on completion, as a client that owns its result
+    memory would do; the pool grows when every buffer of a key is in flight.  Returns
+    the requests that arrived after the warm-up, completed."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t0 = time.monotonic()
     t = 0.0
@@ -319,9 +352,11 @@ def poisson_stream(server: Server, rate: float, duration: float, sizes, accuraci
     outstanding = [0]
     cv = threading.Condition()
 
-    def finished(fut):
-        fut.result()  # raise here if the solve failed; the result itself is dropped
+    def finished(fut, key=None):
+        res = fut.result()  # raise here if the solve failed; the result itself is dropped
         with cv:
+            if outputs is not None:
+                outputs[key].append(res)
             outstanding[0] -= 1
             cv.notify_all()
 
@@ -333,9 +368,14 @@ def poisson_stream(server: Server, rate: float, duration: float, sizes, accuraci
         now = time.monotonic()
         if due > now:
             time.sleep(due - now)
+        out = None
         with cv:
             outstanding[0] += 1
-        server.submit(densities[key], acc, arrival=due).add_done_callback(finished)
+            if outputs is not None:
+                pool = outputs.setdefault(key, [])
+                out = pool.pop() if pool else densities[key].new_empty(densities[key].shape).pin_memory()
+        server.submit(densities[key], acc, arrival=due, out=out).add_done_callback(
+            lambda f, k=key: finished(f, k))
         keys.append((t, key))
         t += float(rng.exponential(1.0 / rate))
     with cv:
@@ -356,8 +396,24 @@ def summarize(completed, t_start: float, t_end: float):
         return None
     lat = sorted((r.done_at - r.arrival) * 1e3 for r in sel)
     span = max(r.done_at for r in sel) - t_start
-    return {"requests": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-            "mean_ms": sum(lat) / len(lat), "solves_per_s": len(lat) / span}
+    by_key = collections.defaultdict(list)
+    for r in sel:
+        key = getattr(r, "key", None)
+        if key is not None:
+            by_key[f"n{key[0]}_{key[1]}"].append((r.done_at - r.arrival) * 1e3)
+    per_key = {k: {"requests": len(v), "p50_ms": percentile(sorted(v), 50), "p99_ms": percentile(sorted(v), 99)}
+               for k, v in sorted(by_key.items())}
+    out = {"requests": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+           "mean_ms": sum(lat) / len(lat), "solves_per_s": len(lat) / span, "by_key": per_key}
+    # split of the latency: waiting for a slot or plan (arrival -> launch) and on the
+    # device (launch -> completion observed)
+    launched = [r for r in sel if getattr(r, "launched_at", None) is not None]
+    if launched:
+        wait = sorted((r.launched_at - r.arrival) * 1e3 for r in launched)
+        run = sorted((r.done_at - r.launched_at) * 1e3 for r in launched)
+        out.update({"wait_p50_ms": percentile(wait, 50), "wait_p99_ms": percentile(wait, 99),
+                    "run_p50_ms": percentile(run, 50), "run_p99_ms": percentile(run, 99)})
+    return out
 
 
 def latency_summary(server: Server, t_start: float, t_end: float):

@@ -63,3 +63,22 @@ def test_budget_bounds_resident_plans_and_bad_request_fails_alone():
         too_big.result(timeout=120)
     srv.stop()
     assert srv.peak_bytes <= int(1.1 * one)
+
+
+def test_results_into_caller_buffers():
+    # results land in the pinned buffers the caller passes; a wrongly shaped buffer fails
+    # its request alone
+    srv = serve.Server(budget_bytes=4e9, max_batch=4, slots=2).start()
+    rhos = [_density(64, i, "df32") for i in range(6)]
+    outs = [torch.full(r.shape, float("nan"), dtype=r.dtype).pin_memory() for r in rhos]
+    futs = [srv.submit(r, 1e-12, out=o) for r, o in zip(rhos, outs)]
+    bad = srv.submit(rhos[0], 1e-12, out=torch.empty((8, 8, 8), dtype=torch.float64))
+    got = [f.result(timeout=120) for f in futs]
+    with pytest.raises(ValueError):
+        bad.result(timeout=120)
+    srv.stop()
+    plan = Plan(64, -1.0, 1.0, precision="df32")
+    for r, o, g in zip(rhos, outs, got):
+        assert g.data_ptr() == o.data_ptr()
+        assert torch.equal(o, plan.solve(r.cuda()).cpu())
+    plan.close()

@@ -59,3 +59,21 @@ def test_batch_cap_by_points():
     assert serve.batch_cap(64, 8, 2 * 256 ** 3) == 8
     # a grid larger than the cap still runs, alone
     assert serve.batch_cap(512, 8, 2 * 256 ** 3) == 1
+
+
+def test_summarize_per_key():
+    Done = serve.Done
+    reqs = [Done(0.1 * i, 0.1 * i + (0.001 if i % 2 else 0.004), (32 if i % 2 else 256, "df32")) for i in range(10)]
+    s = serve.summarize(reqs, 0.0, 1.0)
+    assert set(s["by_key"]) == {"n32_df32", "n256_df32"}
+    assert s["by_key"]["n32_df32"]["requests"] == 5
+    assert abs(s["by_key"]["n256_df32"]["p99_ms"] - 4.0) < 1e-9
+
+
+def test_small_batches_take_high_priority_slots():
+    # slots 0 and 1 are the high-priority streams
+    assert serve.pick_slot([0, 1, 2, 3], 2, small=True) == 0
+    assert serve.pick_slot([0, 1, 2, 3], 2, small=False) == 2
+    assert serve.pick_slot([1, 3], 2, small=True) == 1
+    assert serve.pick_slot([0, 1], 2, small=False) == 0  # no normal slot free: take any
+    assert serve.pick_slot([2], 2, small=True) == 2
