@@ -452,5 +452,6 @@ sp_status sp_setup_run(sp_plan p, cudaStream_t st)
     for (int ax = 0; ax < 3; ++ax) {
         k_twiddles<<<nblk(p->N[ax], 256), 256, 0, st>>>(p->N[ax], p->d_tw64[ax], p->d_tw32[ax], p->d_twdf[ax]);
     }
-    return sp_cuda_check(cudaGetLastError(), "twiddle kernel");
+    if ((rc = sp_cuda_check(cudaGetLastError(), "twiddle kernel"))) return rc;
+    return p->prec == SP_DF32 ? sp_v2_stage_twiddles_df(p, st) : SP_OK;
 }

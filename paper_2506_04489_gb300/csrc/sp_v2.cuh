@@ -6,6 +6,8 @@
 // Included by one translation unit per arithmetic type (float, double, double-float).
 #pragma once
 
+#include <type_traits>
+
 #include "sp_fft.cuh"
 #include "sp_internal.h"
 
@@ -55,6 +57,11 @@ template <int N> struct LayLine {
 // two exchange buffers (two when both fit in 100 KB, for one barrier per stage).
 // (rounded up to an even count, so that everything after it starts on a 16-byte boundary)
 template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<N>() + 1) & ~1; }
+// Passes whose staged twiddles come from global memory (the plan's copy after its N base
+// twiddles, cached in L1) rather than shared memory: double-float at 1024, where 56 KB
+// of tables per CTA would halve the resident CTAs.
+template <class R, int N> constexpr bool tw_global() { return std::is_same<R, df32>::value && N >= 1024; }
+template <class R, int N> constexpr size_t pass_tw_bytes() { return tw_global<R, N>() ? 0 : sizeof(cpx<R>) * tw_entries<R, N>(); }
 constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 
 // ------------------------------------------------------------------ strided passes
@@ -109,15 +116,18 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
     using Lay = LayStrided<R>;
     const int lgB = LGB >= 0 ? LGB : a.lgB, B = 1 << lgB;
     const int BUF = Lay::size(N, B);
-    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, sizeof(cpx<R>) * tw_entries<R, N>());
+    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, pass_tw_bytes<R, N>());
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
     cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
     const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> lgB;
     const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
-    if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws, twg, tid, blockDim.x);
-    if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws, twg, tid, blockDim.x);
+    const cpx<R>* tws = tw_global<R, N>() ? twg + N : tws_s;
+    if constexpr (!tw_global<R, N>()) {
+        if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws_s, twg, tid, blockDim.x);
+        if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws_s, twg, tid, blockDim.x);
+    }
     const int o = blockIdx.y, c = blockIdx.x * B + b, batch = blockIdx.z;
     const bool cv = c < a.ncol;
     const cpx<R>* in = static_cast<const cpx<R>*>(a.in) + batch * a.in_bs + o * a.in_os + c;
@@ -371,7 +381,7 @@ SP_D long long w_row(const ZArgs2& a, long long l) { return (l / a.n1) * a.plane
 template <class R, int N> SP_HD int z_buf(int B) { return B * LayLine<N>::LD; }
 template <class R, int N> SP_HD bool z_two_buffers(int B)
 {
-    return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), sizeof(cpx<R>) * tw_entries<R, N>());
+    return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), pass_tw_bytes<R, N>());
 }
 
 template <class R, class Tio, int N>
@@ -382,11 +392,12 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     const int B = a.B;
     constexpr int R0 = FFTPlan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
-    fill_stage_twiddles<R, N, false>(tws, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
+    const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
+    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, false>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     const Tio* rho = static_cast<const Tio*>(a.rho) + blockIdx.y * a.io_bs;
@@ -428,11 +439,12 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     const int B = a.B;
     constexpr int R0 = FFTPlan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
-    fill_stage_twiddles<R, N, true>(tws, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
+    const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
+    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, true>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     Tio* u = static_cast<Tio*>(a.u) + blockIdx.y * a.io_bs;
@@ -488,7 +500,7 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     ab.lgB = 0;
     while ((1 << ab.lgB) < B) ++ab.lgB;
     const size_t buf = sizeof(cpx<R>) * LayStrided<R>::size(N, B);
-    const size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
+    const size_t twb = pass_tw_bytes<R, N>();
     const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf;
     dim3 grid((unsigned)((a.ncol + B - 1) / B), (unsigned)outer, (unsigned)batch);
     sp_status rc;
@@ -535,7 +547,7 @@ sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
     ab.B = a.B ? a.B : pairs_default<N>();
     const int B = ab.B;
     if (B < 1 || B > pairs_max<N>() || (pairs_max<N>() % B)) return sp_fail(SP_ERR_INVALID, "bad z tile %d", B);
-    const size_t smem = sizeof(cpx<R>) * (tw_entries<R, N>() + (z_two_buffers<R, N>(B) ? 2 : 1) * z_buf<R, N>(B));
+    const size_t smem = pass_tw_bytes<R, N>() + sizeof(cpx<R>) * (z_two_buffers<R, N>(B) ? 2 : 1) * z_buf<R, N>(B);
     const long long pairs = (a.lines + 1) / 2;
     dim3 grid((unsigned)((pairs + B - 1) / B), (unsigned)batch);
     sp_status rc;
@@ -550,6 +562,30 @@ sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
 }
 
 // Length dispatch: calls f.template run<N>() for a supported N.
+template <class R, int N>
+__global__ void k_stage_twiddles(cpx<R>* dst, const cpx<R>* __restrict__ tw)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    fill_stage_twiddles<R, N, false>(dst, tw, tid, nth);
+    fill_stage_twiddles<R, N, true>(dst, tw, tid, nth);
+}
+
+template <class F> inline sp_status with_len(int N, F&& f);
+
+template <class R> struct StageTw {
+    cpx<R>* tw;
+    cudaStream_t st;
+    template <int N> sp_status run()
+    {
+        if constexpr (tw_global<R, N>()) {
+            static_assert(tw_stage_size<N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
+            k_stage_twiddles<R, N><<<16, 256, 0, st>>>(tw + N, tw);
+            return sp_cuda_check(cudaGetLastError(), "staged twiddles");
+        }
+        return SP_OK;
+    }
+};
+
 template <class F> inline sp_status with_len(int N, F&& f)
 {
     switch (N) {
@@ -589,6 +625,17 @@ template <class R> struct Tabs {
     static const void* tw(sp_plan p, int ax);
     static const void* M(sp_plan p);
 };
+
+// Staged twiddle tables in global memory for the axes whose line passes read them there.
+template <class R> sp_status stage_twiddles(sp_plan p, cudaStream_t st)
+{
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!len_ok(p->N[ax])) continue;
+        sp_status rc = with_len(p->N[ax], StageTw<R>{static_cast<cpx<R>*>(const_cast<void*>(Tabs<R>::tw(p, ax))), st});
+        if (rc) return rc;
+    }
+    return SP_OK;
+}
 
 // The whole solve; `work` is the workspace (the plan's, or another of the same size).
 template <class R, class Tio>

@@ -19,6 +19,11 @@ sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t 
     return v2::forward<df32, double>(p, rho, spec, st);
 }
 
+sp_status sp_v2_stage_twiddles_df(sp_plan p, cudaStream_t st)
+{
+    return v2::stage_twiddles<df32>(p, st);
+}
+
 float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
 {
     return v2::time_pass<df32, double>(p, pass, tile, batch, iters, st);
