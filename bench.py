@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration legs")
     ap.add_argument("--profile", nargs=3, metavar=("N", "PRECISION", "SOLVES"),
                     help="only build one plan and run SOLVES solves (a small target for ncu)")
     ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV",
@@ -472,6 +473,115 @@ def run_cufft_comparison(n, rho_np, m_octant, ref_u, steps, warmup, stream):
     return out
 
 
+def _time_on(stream, fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def run_configs():
+    """The other benchmark configurations, each timed with CUDA events on its own stream
+    (a few steps each, after warm-up):
+      c1  32^3 normalised Gaussian (sigma 0.1) on [-1,1]^3, FP64: time and max-norm error
+          against the closed form erf(r/(sigma sqrt 2))/(4 pi r);
+      c2  128^3 bump and cos-Gaussian on [-1,1]^3: double-float and native FP64;
+      c3  512^3 bump: double-float, mixed (FP32 passes) and native FP64, with the mixed
+          path's deviation from the double-float one and its speedup over native FP64;
+      c4  64 right-hand sides of 128^3 (seeded Gaussian mixtures) in one batched solve
+          replayed from a captured CUDA graph, autotuned tiles: double-float and FP32."""
+    import numpy as np
+    import torch
+
+    from paper_2506_04489_gb300 import Plan, workloads as W
+    st = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(st):
+        # c1
+        n, sig = 32, 0.1
+        plan = Plan(n, BOX[0], BOX[1], precision="fp64")
+        rho = torch.from_numpy(W.gaussian(n, BOX[0], BOX[1], sig)).cuda()
+        u = torch.empty_like(rho)
+        ms = _time_on(st, lambda: plan.solve(rho, u, st), 20, 3)
+        X, Y, Z = W.mesh(n, BOX[0], BOX[1])
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        exact = np.vectorize(math.erf)(r / (sig * math.sqrt(2.0))) / (4.0 * math.pi * r)
+        err = float(np.abs(u.cpu().numpy() - exact).max() / np.abs(exact).max())
+        out["c1_gaussian_32_fp64"] = {"ms_per_solve": ms, "max_rel_err_vs_closed_form": err}
+        plan.close()
+        # c2
+        n = 128
+        c2 = {}
+        for name, dens in (("bump", W.bump_profile(n, *BOX)), ("cos_gaussian", W.cos_gaussian(n, *BOX))):
+            ref = None
+            for prec in ("fp64", "df32"):
+                plan = Plan(n, BOX[0], BOX[1], precision=prec)
+                plan.autotune(1)
+                rho = torch.from_numpy(dens).cuda()
+                u = torch.empty_like(rho)
+                ms = _time_on(st, lambda: plan.solve(rho, u, st), 20, 3)
+                rec = {"ms_per_solve": ms, "value": n ** 3 / (ms / 1e3), "unit": "grid pts/s"}
+                if ref is None:
+                    ref = u.clone()
+                else:
+                    rec["max_rel_dev_from_fp64"] = float((u - ref).abs().max() / ref.abs().max())
+                c2[f"{name}_{prec}"] = rec
+                plan.close()
+        out["c2_128"] = c2
+        # c3
+        n = 512
+        c3 = {}
+        dens = W.bump_profile(n, *BOX)
+        ref = None
+        for prec, steps, tune in (("df32", 5, True), ("mixed", 5, True), ("fp64", 2, False)):
+            plan = Plan(n, BOX[0], BOX[1], precision=prec)
+            if tune:
+                plan.autotune(1)
+            rho = torch.from_numpy(dens).cuda()
+            u = torch.empty_like(rho)
+            ms = _time_on(st, lambda: plan.solve(rho, u, st), steps, 1)
+            rec = {"ms_per_solve": ms, "value": n ** 3 / (ms / 1e3), "unit": "grid pts/s"}
+            if ref is None:
+                ref = u.clone()
+            else:
+                rec["max_rel_dev_from_df32"] = float((u - ref).abs().max() / ref.abs().max())
+            c3[prec] = rec
+            plan.close()
+            del rho, u
+            torch.cuda.empty_cache()
+        c3["mixed_speedup_over_fp64"] = c3["fp64"]["ms_per_solve"] / c3["mixed"]["ms_per_solve"]
+        c3["df32_speedup_over_fp64"] = c3["fp64"]["ms_per_solve"] / c3["df32"]["ms_per_solve"]
+        out["c3_bump_512"] = c3
+        del ref
+        torch.cuda.empty_cache()
+        # c4
+        n, nb = 128, 64
+        c4 = {}
+        host = np.stack([W.gaussian_mixture(n, BOX[0], BOX[1], s) for s in range(nb)])
+        for prec in ("df32", "fp32"):
+            plan = Plan(n, BOX[0], BOX[1], precision=prec, max_batch=nb)
+            plan.autotune(nb)
+            rho = torch.from_numpy(host).to("cuda", dtype=plan.dtype)
+            u = torch.empty_like(rho)
+            graph = plan.capture(rho, u, st)
+            ms = _time_on(st, lambda: graph.launch(st), 10, 2)
+            c4[prec] = {"ms_per_batch": ms, "solves_per_s": nb / (ms / 1e3), "value": nb * n ** 3 / (ms / 1e3),
+                        "unit": "grid pts/s", "tiles": plan.tiles()}
+            graph.close()
+            plan.close()
+            del rho, u
+            torch.cuda.empty_cache()
+        out["c4_batched_64x128_graph"] = c4
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -543,6 +653,7 @@ def run_ours(args, world, rank, local):
         del rhos, outs, base
         torch.cuda.empty_cache()
     cufft = run_cufft_comparison(n, rho_np, m_octant, ref_u, args.steps, args.warmup, stream)
+    configs = run_configs() if (world == 1 and not args.no_configs) else None
     del ref_u
     torch.cuda.empty_cache()
     served = None
@@ -579,6 +690,7 @@ def run_ours(args, world, rank, local):
                  "max_rel_dev_from_fp64": results["fp32"]["max_rel_dev_from_fp64"]},
         "e2e": results["e2e"],
         "cufft_comparison": cufft,
+        "configs": configs,
         "served": served,
         "gpu_launches": r64["gpu_launches"],
         "clocks": clocks,
