@@ -162,9 +162,10 @@ template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 // lay(8 j + q) = lay(8 j) + q * lay.unit for q < 8: the stage loops then compute one
 // slot per butterfly and add compile-time offsets for the others.
 
-// Per-stage twiddle tables in shared memory: stage s (span P > 1, radix RAD) keeps
-// w^{r k N/(P RAD)} at [k (RAD + 1) + r], so a butterfly reads RAD - 1 consecutive
-// entries; the extra entry per row puts the rows of neighbouring k on different banks.
+// Per-stage twiddle tables (in shared memory; for double-float, one copy per plan in
+// global memory): stage s (span P > 1, radix RAD) keeps w^{r k N/(P RAD)} at
+// [k (RAD + 1) + r], so a butterfly reads RAD - 1 consecutive entries; the extra entry
+// per row puts the rows of neighbouring k on different banks.
 template <int N, bool INV> constexpr int tw_stage_offset(int s)
 {
     int off = 0;

@@ -53,9 +53,10 @@ template <int N> struct LayLine {
     SP_D int step(int d) const { return d + d / 8; }
 };
 
-// Shared memory of a pass: the staged twiddles of the directions it runs, then one or
-// two exchange buffers (two when both fit in 100 KB, for one barrier per stage).
-// (rounded up to an even count, so that everything after it starts on a 16-byte boundary)
+// Shared memory of a pass: the staged twiddles of the directions it runs (unless they
+// are read from global memory, below), then one or two exchange buffers (two when both
+// fit in 100 KB, for one barrier per stage).  The twiddle entry count is rounded up to
+// an even count, so that everything after it starts on a 16-byte boundary.
 template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<N>() + 1) & ~1; }
 // Passes whose staged twiddles come from global memory (the plan's copy after its N base
 // twiddles, cached in L1) rather than shared memory: double-float, whose tables (21 KB
