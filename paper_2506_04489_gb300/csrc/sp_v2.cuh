@@ -6,6 +6,7 @@
 // Included by one translation unit per arithmetic type (float, double, double-float).
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "sp_fft.cuh"
@@ -479,15 +480,21 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
 }
 
 // ------------------------------------------------------------------ launchers
-// Raise one kernel's dynamic shared-memory limit once, to more than any of its launches
-// uses, so that later launches (e.g. under stream capture) make no attribute call.
+// Raise one kernel's dynamic shared-memory limit once per device (the attribute is a
+// per-device setting), to more than any of its launches uses, so that later launches
+// (e.g. under stream capture) make no attribute call.
 template <auto KERNEL> inline sp_status smem_attr(size_t bytes)
 {
-    static bool done = false;
-    if (done || bytes <= 48 * 1024) return SP_OK;
-    sp_status rc = sp_cuda_check(cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-                                 "set shared memory size");
-    if (rc == SP_OK) done = true;
+    static std::atomic<unsigned long long> done{0};  // bit d: set on device d
+    if (bytes <= 48 * 1024) return SP_OK;
+    int dev = 0;
+    sp_status rc = sp_cuda_check(cudaGetDevice(&dev), "current device");
+    if (rc) return rc;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return SP_OK;
+    rc = sp_cuda_check(cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                       "set shared memory size");
+    if (rc == SP_OK) done.fetch_or(bit, std::memory_order_relaxed);
     return rc;
 }
 
@@ -513,13 +520,12 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
                               (a.in_os * sizeof(cpx<R>)) % 16 == 0 && (a.in_bs * sizeof(cpx<R>)) % 16 == 0;
     if (ab.lgB == lg_default<N>() && psmem <= 110 * 1024 && rows_aligned && (a.ncol + B - 1) / B * B <= a.in_ld) {
         if ((rc = smem_attr<k3_line<R, N, MODE>>(psmem))) return rc;
-        static int per_sm = 0;
+        static std::atomic<int> per_sm_cached{0};  // resident CTAs per SM (same on every GB300)
+        int per_sm = per_sm_cached.load(std::memory_order_relaxed);
         if (!per_sm) {
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_line<R, N, MODE>, (N / E) * B, psmem);
             if (per_sm < 1) per_sm = 1;
-            (void)sms;
+            per_sm_cached.store(per_sm, std::memory_order_relaxed);
         }
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
