@@ -182,6 +182,12 @@ class Plan:
         its own, two device buffers per direction.  Returns after the last result is on
         the host."""
         import torch
+        if len(inputs) != len(outputs):
+            raise ValueError("inputs and outputs must have the same length")
+        for t in list(inputs) + list(outputs):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != self.n \
+                    or not t.is_contiguous():
+                raise ValueError(f"expected contiguous CPU {self.dtype} tensors of shape {self.n}")
         solve_st = stream if stream is not None else torch.cuda.current_stream()
         if getattr(self, "_copy_streams", None) is None:
             self._copy_streams = (torch.cuda.Stream(), torch.cuda.Stream())

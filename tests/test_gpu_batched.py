@@ -86,4 +86,14 @@ def test_host_stream_matches_device_solves(rhs, precision):
     plan.solve_host_stream([ins[2]] * 3, outs2)
     for o in outs2:
         assert torch.equal(o, outs[2])
+    # wrong dtype, wrong shape, device tensors and unequal lengths are rejected
+    other = torch.float64 if plan.dtype == torch.float32 else torch.float32
+    with pytest.raises(ValueError):
+        plan.solve_host_stream([ins[0].to(other)], [outs[0]])
+    with pytest.raises(ValueError):
+        plan.solve_host_stream([ins[0][:-1]], [outs[0]])
+    with pytest.raises(ValueError):
+        plan.solve_host_stream([ins[0].cuda()], [outs[0]])
+    with pytest.raises(ValueError):
+        plan.solve_host_stream(ins[:2], outs[:1])
     plan.close()
