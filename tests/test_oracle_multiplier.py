@@ -9,6 +9,7 @@ scaling fails.
 import math
 
 import numpy as np
+import pytest
 
 
 def brute_vhat(k, L, w, a, q=72):
@@ -47,3 +48,21 @@ def test_multiplier_zero_mode_and_symmetry(oracle):
     # a cube: M is symmetric under any permutation of the three wavenumbers
     np.testing.assert_allclose(M, M.transpose(1, 0, 2), rtol=1e-13, atol=1e-16 * np.abs(M).max())
     np.testing.assert_allclose(M, M.transpose(2, 1, 0), rtol=1e-13, atol=1e-16 * np.abs(M).max())
+
+
+@pytest.mark.parametrize("n,lo,hi", [((32, 32, 32), (-1, -1, -1), (1, 1, 1)),
+                                     ((24, 32, 20), (-1, -2, -0.5), (1.5, 1, 1))])
+def test_multiplier_asymptote(oracle, n, lo, hi):
+    # Away from the axes (every |k_p| >= 4) the window and the GS cutoff barely matter
+    # and M tends to the Fourier transform of the Newton kernel 1/(4 pi |x|): M |kappa|^2
+    # -> 1 (a loose asymptote, but one no plausible mistake satisfies).  A wrong kappa scale, a missing normalisation or a
+    # dropped rank-3 term of V_hat moves the ratio far from 1.
+    _, L = oracle.geometry(n, lo, hi)
+    _, _, M = oracle.plan_tables(n, lo, hi)
+    k = [np.arange(m + 1) for m in n]
+    kap2 = ((math.pi * k[0] / L[0]) ** 2)[:, None, None] + ((math.pi * k[1] / L[1]) ** 2)[None, :, None] + \
+        ((math.pi * k[2] / L[2]) ** 2)[None, None, :]
+    kmin = np.minimum(np.minimum(k[0][:, None, None], k[1][None, :, None]), k[2][None, None, :])
+    r = (M * kap2)[kmin >= 4]
+    assert np.median(np.abs(r - 1)) < 2e-3
+    assert np.abs(r - 1).max() < 0.05
