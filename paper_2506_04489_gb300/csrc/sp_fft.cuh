@@ -15,6 +15,8 @@
 // last stage.  Both are pruned at compile time.
 #pragma once
 
+#include <type_traits>
+
 #include "sp_common.cuh"
 #include "sp_df32.cuh"
 
@@ -225,9 +227,25 @@ template <class R, int N, bool INV, int ST> struct Stage {
             if constexpr (P > 1) {
                 const int k = (t + T * m) % P;
                 const cpx<R>* w = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST) + k * (RAD + 1);
+                if constexpr (std::is_same<R, float>::value && RAD == 8) {
+                    // FP32: w^2, w^3, w^5, w^6, w^7 from the loaded w and w^4 (two table reads
+                    // instead of seven; a few ulps more twiddle error, far below FP32's bar)
+                    cpx<R> ww[8];
+                    ww[1] = w[1];
+                    ww[4] = w[4];
+                    ww[2] = cmul(ww[1], ww[1]);
+                    ww[3] = cmul(ww[1], ww[2]);
+                    ww[5] = cmul(ww[4], ww[1]);
+                    ww[6] = cmul(ww[4], ww[2]);
+                    ww[7] = cmul(ww[4], ww[3]);
 #pragma unroll
-                for (int r = 1; r < RAD; ++r)
-                    v[m * RAD + r] = S < 0 ? tw_mul(v[m * RAD + r], w[r]) : tw_mulc(v[m * RAD + r], w[r]);
+                    for (int r = 1; r < RAD; ++r)
+                        v[m * RAD + r] = S < 0 ? tw_mul(v[m * RAD + r], ww[r]) : tw_mulc(v[m * RAD + r], ww[r]);
+                } else {
+#pragma unroll
+                    for (int r = 1; r < RAD; ++r)
+                        v[m * RAD + r] = S < 0 ? tw_mul(v[m * RAD + r], w[r]) : tw_mulc(v[m * RAD + r], w[r]);
+                }
             }
             butterfly<RAD, S, HALF>(&v[m * RAD]);
         }
