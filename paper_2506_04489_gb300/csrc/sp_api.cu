@@ -155,7 +155,7 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     if (prec == SP_DF32) SP_ALLOC(p->d_Mdf, sizeof(df32) * mcount);
     for (int ax = 0; ax < 3; ++ax) {
         SP_ALLOC(p->d_tw64[ax], sizeof(cpx<double>) * p->N[ax]);
-        SP_ALLOC(p->d_tw32[ax], sizeof(cpx<float>) * p->N[ax]);
+        SP_ALLOC(p->d_tw32[ax], sizeof(cpx<float>) * (p->N[ax] + SP_TW_STAGED_MAX));
         SP_ALLOC(p->d_twdf[ax], sizeof(cpx<df32>) * (p->N[ax] + SP_TW_STAGED_MAX));
     }
     const size_t csize = (prec == SP_FP64 || prec == SP_DF32) ? 16 : 8;

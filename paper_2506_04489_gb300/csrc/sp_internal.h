@@ -81,11 +81,12 @@ sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t
 sp_status sp_v2_forward_f64(sp_plan p, const void* rho, void* spec, cudaStream_t st);
 sp_status sp_v2_forward_df(sp_plan p, const void* rho, void* spec, cudaStream_t st);
 bool sp_v2_supported(int N);
-// Double-float plans keep, after the N base twiddles of an axis, the per-stage twiddle
-// tables that their passes read from global memory; room for this many entries is
-// reserved.
+// Double-float and FP32 plans keep, after the N base twiddles of an axis, the per-stage
+// twiddle tables that their passes read from global memory; room for this many entries
+// is reserved.
 #define SP_TW_STAGED_MAX 4096
 sp_status sp_v2_stage_twiddles_df(sp_plan p, cudaStream_t st);
+sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st);
 float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed);
 float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
 float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);

@@ -453,5 +453,7 @@ sp_status sp_setup_run(sp_plan p, cudaStream_t st)
         k_twiddles<<<nblk(p->N[ax], 256), 256, 0, st>>>(p->N[ax], p->d_tw64[ax], p->d_tw32[ax], p->d_twdf[ax]);
     }
     if ((rc = sp_cuda_check(cudaGetLastError(), "twiddle kernel"))) return rc;
-    return p->prec == SP_DF32 ? sp_v2_stage_twiddles_df(p, st) : SP_OK;
+    if (p->prec == SP_DF32) return sp_v2_stage_twiddles_df(p, st);
+    if (p->prec == SP_FP32 || p->prec == SP_MIXED) return sp_v2_stage_twiddles_f32(p, st);
+    return SP_OK;
 }

@@ -62,8 +62,9 @@ template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<N>(
 // Passes whose staged twiddles come from global memory (the plan's copy after its N base
 // twiddles, cached in L1) rather than shared memory: double-float, whose tables (21 KB
 // per CTA at 512, 56 KB at 1024) limit the resident CTAs and cost a fill per CTA
-// (measured: 8 % faster at 128^3, 5 % at 256^3, 17 % at 512^3).
-template <class R, int N> constexpr bool tw_global() { return std::is_same<R, df32>::value; }
+// (measured: 8 % faster at 128^3, 5 % at 256^3, 17 % at 512^3), and FP32 (its z passes
+// 20-30 % faster).  The pipelined line kernel keeps its tables in shared memory.
+template <class R, int N> constexpr bool tw_global() { return std::is_same<R, df32>::value || std::is_same<R, float>::value; }
 template <class R, int N> constexpr size_t pass_tw_bytes() { return tw_global<R, N>() ? 0 : sizeof(cpx<R>) * tw_entries<R, N>(); }
 constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 

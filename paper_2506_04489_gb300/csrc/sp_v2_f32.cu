@@ -23,3 +23,8 @@ float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, c
 {
     return mixed ? v2::time_pass<float, double>(p, pass, tile, batch, iters, st) : v2::time_pass<float, float>(p, pass, tile, batch, iters, st);
 }
+
+sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st)
+{
+    return v2::stage_twiddles<float>(p, st);
+}
