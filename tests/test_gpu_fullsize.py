@@ -127,3 +127,20 @@ def test_spectral_laplacian_returns_the_potential(n):
         E = float((u - ustar).abs().max() / ustar.abs().max())
         assert E < tol, (precision, E)
         plan.close()
+
+
+@pytest.mark.parametrize("precision", ["df32", "fp32", "fp64"])
+def test_benchmark_launch_configuration_bitwise(precision):
+    # The benchmark autotunes the tiles (and so runs other kernels: runtime tiles, the
+    # pipelined line kernel) before timing; the full-size parity above uses the default
+    # tiles.  Tiles only regroup lines into CTAs, so the 256^3 results must agree bit for
+    # bit, which carries every full-size check over to the timed configuration.
+    n = 256
+    plan = Plan(n, LO, HI, precision=precision)
+    rho = _bump(n).cuda().to(plan.dtype)
+    before = plan.solve(rho)
+    tiles = plan.autotune(1)
+    after = plan.solve(rho)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after), tiles
+    plan.close()
