@@ -20,6 +20,9 @@
  * Conventions shared by every entry point:
  *   - Arrays are C order [x][y][z] (z fastest), n0 x n1 x n2 elements.
  *   - Device pointers are CUDA device (or managed) memory of the current device.
+ *   - A plan belongs to the device that was current at sp_plan_create; every call on it
+ *     except sp_plan_destroy must be made with that device current (else
+ *     SP_ERR_INVALID, naming both devices).
  *   - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.
  *     All work is stream-ordered; no entry point below synchronises the host unless
  *     it says so.
@@ -130,8 +133,9 @@ sp_status sp_solve(sp_plan plan, const void* rho, void* u, sp_stream stream);
 sp_status sp_solve_batched(sp_plan plan, const void* rho, void* u, int batch,
                            sp_stream stream);
 
-/* sp_plan_destroy -- wait for the plan's outstanding work (device synchronise) and free
- * everything it owns.  NULL is accepted. */
+/* sp_plan_destroy -- wait for the plan's outstanding work (synchronise the plan's device)
+ * and free everything it owns, from any current device (the current device is left as it
+ * was).  NULL is accepted. */
 sp_status sp_plan_destroy(sp_plan plan);
 
 /* Bytes of device workspace the plan holds for solves (0 for a NULL plan). */

@@ -180,7 +180,8 @@ extern "C" sp_status sp_kernel_precompute(sp_plan p, sp_stream stream)
     g_err[0] = 0;
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    sp_status rc;
+    sp_status rc = sp_check_device(p);
+    if (rc) return rc;
     const size_t mcount = (size_t)(p->n[0] + 1) * (p->n[1] + 1) * p->ldz;
     if ((rc = sp_cuda_check(cudaMemsetAsync(p->d_M64, 0, sizeof(double) * mcount, st), "clear multiplier")))
         return rc;
@@ -200,12 +201,24 @@ extern "C" sp_status sp_plan_set_kernel(sp_plan p, sp_kernel kind)
     return SP_OK;
 }
 
+// The plan's memory lives on the device it was created on; launching its passes while
+// another device is current would hand that device foreign pointers.
+sp_status sp_check_device(const sp_plan p)
+{
+    int dev = -1;
+    sp_status rc = sp_cuda_check(cudaGetDevice(&dev), "current device");
+    if (rc) return rc;
+    if (dev != p->device)
+        return sp_fail(SP_ERR_INVALID, "plan was created on device %d, current device is %d", p->device, dev);
+    return SP_OK;
+}
+
 static sp_status check_solve_args(sp_plan p, const void* rho, const void* u)
 {
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
     if (!rho || !u) return sp_fail(SP_ERR_INVALID, "rho and u must be non-NULL device pointers");
     if (!p->ready) return sp_fail(SP_ERR_NOT_READY, "sp_kernel_precompute has not been run on this plan");
-    return SP_OK;
+    return sp_check_device(p);
 }
 
 extern "C" sp_status sp_solve(sp_plan p, const void* rho, void* u, sp_stream stream)
@@ -238,8 +251,13 @@ extern "C" sp_status sp_plan_destroy(sp_plan p)
 {
     g_err[0] = 0;
     if (!p) return SP_OK;
+    // wait for and free on the plan's own device, whichever device is current
+    int cur = -1;
+    const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
+                          cudaSetDevice(p->device) == cudaSuccess;
     cudaError_t e = cudaDeviceSynchronize();
     free_plan(p);
+    if (switched) cudaSetDevice(cur);
     return sp_cuda_check(e, "synchronise before destroy");
 }
 

@@ -34,6 +34,7 @@ extern "C" sp_status sp_plan_autotune(sp_plan p, int batch, sp_stream stream)
     if (!p->ready) return sp_fail(SP_ERR_NOT_READY, "sp_kernel_precompute has not been run on this plan");
     if (batch < 1 || batch > p->max_batch)
         return sp_fail(SP_ERR_INVALID, "batch %d outside [1, max_batch = %d]", batch, p->max_batch);
+    if (sp_status rc = sp_check_device(p)) return rc;
     for (int ax = 0; ax < 3; ++ax)
         if (!sp_v2_supported(p->N[ax])) return SP_OK;  // first-generation passes: nothing to tune
     cudaStream_t st = (cudaStream_t)stream;
@@ -79,6 +80,7 @@ extern "C" sp_status sp_graph_capture(sp_plan p, const void* rho, void* u, int b
     if (batch < 1 || batch > p->max_batch)
         return sp_fail(SP_ERR_INVALID, "batch %d outside [1, max_batch = %d]", batch, p->max_batch);
     if (!stream) return sp_fail(SP_ERR_INVALID, "graph capture needs a created stream, not the legacy default");
+    if (sp_status rc0 = sp_check_device(p)) return rc0;
     cudaStream_t st = (cudaStream_t)stream;
     // one eager solve first: it sets every kernel attribute outside the capture
     sp_plan_s view = *p;

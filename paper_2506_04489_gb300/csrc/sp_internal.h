@@ -68,6 +68,7 @@ sp_status sp_mark(sp_plan p, cudaStream_t st);
 void sp_clear_error(void);
 sp_status sp_fail(sp_status st, const char* fmt, ...);
 sp_status sp_cuda_check(cudaError_t e, const char* what);
+sp_status sp_check_device(const sp_plan p);  // SP_ERR_INVALID unless p's device is current
 
 // Setup (sp_setup.cu).  All FP64.
 sp_status sp_setup_run(sp_plan p, cudaStream_t st);
