@@ -103,10 +103,16 @@ def minimal_bytes_per_point(prec):
     return 152.0 if prec in ("fp64", "df32") else 76.0
 
 
+# Sources of the solve-pass kernels (the plan, setup, graph and API files do not change
+# what a pass executes); ncu counts are valid while their hash is unchanged.
+PASS_SOURCES = ("sp_common.cuh", "sp_df32.cuh", "sp_fft.cuh", "sp_v2.cuh", "sp_passes.cu", "sp_v2_df.cu",
+                "sp_v2_df_lines.cu", "sp_v2_f32.cu", "sp_v2_f32_lines.cu", "sp_v2_f64.cu", "sp_v2_f64_lines.cu")
+
+
 def source_hash():
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2506_04489_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in PASS_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
