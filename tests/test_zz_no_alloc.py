@@ -19,7 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+TOL = {"fp64": 1e-12, "df32": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
 
 
 def _noalloc(native, plan, rho, u):
@@ -29,7 +29,8 @@ def _noalloc(native, plan, rho, u):
 
 
 @pytest.mark.parametrize("precision,n", [("fp64", (48, 64, 36)), ("fp64", (96, 96, 96)),
-                                         ("fp32", (128, 128, 128)), ("mixed", (64, 64, 64))])
+                                         ("fp32", (128, 128, 128)), ("mixed", (64, 64, 64)),
+                                         ("df32", (64, 96, 64))])
 def test_noalloc_matches_solve_twice(precision, n):
     from paper_2506_04489_gb300 import Plan, _native, workloads as W
     plan = Plan(n, (-1.0, -1.2, -0.8), (1.0, 1.2, 0.9), precision=precision)
