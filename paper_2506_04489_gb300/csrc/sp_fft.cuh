@@ -57,7 +57,7 @@ template <class R> SP_D cpx<R> norm(cpx<R> a) { return a; }
 template <> SP_D cpx<df32> norm<df32>(cpx<df32> a) { return df_norm_c(a); }
 
 // ------------------------------------------------------------------ plans
-// Forward radices: powers of two first (the first stage is radix 8, so zero padding
+// Forward radices: powers of two first (the first stage is radix 8 or 16, so zero padding
 // prunes it uniformly), then 3s.  E is a multiple of every radix.
 template <int N> struct FFTPlan;
 template <> struct FFTPlan<64> { static constexpr int NS = 2, E = 8; static constexpr int R[2] = {8, 8}; };
@@ -68,15 +68,27 @@ template <> struct FFTPlan<384> { static constexpr int NS = 4, E = 24; static co
 template <> struct FFTPlan<512> { static constexpr int NS = 3, E = 8; static constexpr int R[3] = {8, 8, 8}; };
 template <> struct FFTPlan<1024> { static constexpr int NS = 4, E = 8; static constexpr int R[4] = {8, 8, 8, 2}; };
 
+// The plan a pass of arithmetic type R uses.  At 1024, FP32 and FP64 take a radix-16
+// first stage (16 values a thread, three stages: one exchange fewer, 15 % faster at
+// 512^3 in FP32); double-float keeps eight values a thread, whose 16-value form holds
+// too many registers (measured 6 % slower).
+struct Plan1024Radix16 {
+    static constexpr int NS = 3, E = 16;
+    static constexpr int R[3] = {16, 8, 8};
+};
+template <class R, int N> struct PlanOf : FFTPlan<N> {};
+template <> struct PlanOf<float, 1024> : Plan1024Radix16 {};
+template <> struct PlanOf<double, 1024> : Plan1024Radix16 {};
+
 // radix of stage s of the forward (INV = false) or inverse (reversed) transform
-template <int N, bool INV> constexpr int radix_at(int s)
+template <class R, int N, bool INV> constexpr int radix_at(int s)
 {
-    return INV ? FFTPlan<N>::R[FFTPlan<N>::NS - 1 - s] : FFTPlan<N>::R[s];
+    return INV ? PlanOf<R, N>::R[PlanOf<R, N>::NS - 1 - s] : PlanOf<R, N>::R[s];
 }
-template <int N, bool INV> constexpr int span_at(int s)
+template <class R, int N, bool INV> constexpr int span_at(int s)
 {
     int p = 1;
-    for (int i = 0; i < s; ++i) p *= radix_at<N, INV>(i);
+    for (int i = 0; i < s; ++i) p *= radix_at<R, N, INV>(i);
     return p;
 }
 
@@ -144,9 +156,62 @@ template <int S, class R> SP_D void bf8_half(cpx<R>* u)
     bf8_tail<S>(u, a0 + a2, a0 + a3, a0 - a2, a0 - a3, b0 + b2, b0 + b3, b0 - b2, b0 - b3);
 }
 
+// radix 16 as 2 x 8: the DFTs of the even and odd halves, then
+// X_q = E_q + w^q O_q, X_{q+8} = E_q - w^q O_q with w = exp(S 2 pi i / 16).
+template <int S, class R> SP_D void bf16_tail(cpx<R>* u, cpx<R>* e, cpx<R>* o)
+{
+    const R h = Num<R>::c(0.70710678118654752440084436210484904);   // cos(pi/4)
+    const R c1 = Num<R>::c(0.92387953251128675612818318939678829);  // cos(pi/8)
+    const R s1 = Num<R>::c(0.38268343236508977172845998403039887);  // sin(pi/8)
+    cpx<R> t[8];
+    t[0] = o[0];
+    t[1] = tw_mul(o[1], mk(c1, S > 0 ? s1 : -s1));
+    t[2] = scale(o[2] + mul_si<S>(o[2]), h);
+    t[3] = tw_mul(o[3], mk(s1, S > 0 ? c1 : -c1));
+    t[4] = mul_si<S>(o[4]);
+    t[5] = tw_mul(o[5], mk(-s1, S > 0 ? c1 : -c1));
+    t[6] = scale(mul_si<S>(o[6]) - o[6], h);
+    t[7] = tw_mul(o[7], mk(-c1, S > 0 ? s1 : -s1));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        u[q] = e[q] + t[q];
+        u[q + 8] = e[q] - t[q];
+    }
+}
+
+template <int S, class R> SP_D void bf16(cpx<R>* u)
+{
+    cpx<R> e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        e[j] = u[2 * j];
+        o[j] = u[2 * j + 1];
+    }
+    bf8<S>(e);
+    bf8<S>(o);
+    bf16_tail<S>(u, e, o);
+}
+
+// radix 16 with u[8..15] = 0: both halves have their upper four inputs zero
+template <int S, class R> SP_D void bf16_half(cpx<R>* u)
+{
+    cpx<R> e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        e[j] = u[2 * j];
+        o[j] = u[2 * j + 1];
+    }
+    bf8_half<S>(e);
+    bf8_half<S>(o);
+    bf16_tail<S>(u, e, o);
+}
+
 template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 {
-    if constexpr (RAD == 8) {
+    if constexpr (RAD == 16) {
+        if constexpr (HALF) bf16_half<S>(u);
+        else bf16<S>(u);
+    } else if constexpr (RAD == 8) {
         if constexpr (HALF) bf8_half<S>(u);
         else bf8<S>(u);
     } else if constexpr (RAD == 4) {
@@ -168,28 +233,28 @@ template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 // global memory): stage s (span P > 1, radix RAD) keeps w^{r k N/(P RAD)} at
 // [k (RAD + 1) + r], so a butterfly reads RAD - 1 consecutive entries; the extra entry
 // per row puts the rows of neighbouring k on different banks.
-template <int N, bool INV> constexpr int tw_stage_offset(int s)
+template <class R, int N, bool INV> constexpr int tw_stage_offset(int s)
 {
     int off = 0;
     for (int i = 0; i < s; ++i)
-        if (span_at<N, INV>(i) > 1) off += span_at<N, INV>(i) * (radix_at<N, INV>(i) + 1);
+        if (span_at<R, N, INV>(i) > 1) off += span_at<R, N, INV>(i) * (radix_at<R, N, INV>(i) + 1);
     return off;
 }
-template <int N> constexpr int tw_stage_size()
+template <class R, int N> constexpr int tw_stage_size()
 {
-    return tw_stage_offset<N, false>(FFTPlan<N>::NS) + tw_stage_offset<N, true>(FFTPlan<N>::NS);
+    return tw_stage_offset<R, N, false>(PlanOf<R, N>::NS) + tw_stage_offset<R, N, true>(PlanOf<R, N>::NS);
 }
-template <int N, bool INV> constexpr int tw_base() { return INV ? tw_stage_offset<N, false>(FFTPlan<N>::NS) : 0; }
+template <class R, int N, bool INV> constexpr int tw_base() { return INV ? tw_stage_offset<R, N, false>(PlanOf<R, N>::NS) : 0; }
 
 // Fill the staged tables (all threads of the block; a barrier must follow).
 template <class R, int N, bool INV, int ST = 0>
 SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int tid, int nthreads)
 {
-    if constexpr (ST < FFTPlan<N>::NS) {
-        constexpr int P = span_at<N, INV>(ST), RAD = radix_at<N, INV>(ST);
+    if constexpr (ST < PlanOf<R, N>::NS) {
+        constexpr int P = span_at<R, N, INV>(ST), RAD = radix_at<R, N, INV>(ST);
         if constexpr (P > 1) {
             constexpr int TWS = N / (P * RAD);
-            cpx<R>* dst = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST);
+            cpx<R>* dst = tws + tw_base<R, N, INV>() + tw_stage_offset<R, N, INV>(ST);
             for (int j = tid; j < P * RAD; j += nthreads) {
                 const int k = j / RAD, r = j % RAD;
                 dst[k * (RAD + 1) + r] = tw[r * k * TWS];
@@ -200,10 +265,10 @@ SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int ti
 }
 
 template <class R, int N, bool INV, int ST> struct Stage {
-    static constexpr int E = FFTPlan<N>::E;
+    static constexpr int E = PlanOf<R, N>::E;
     static constexpr int T = N / E;
-    static constexpr int RAD = radix_at<N, INV>(ST);
-    static constexpr int P = span_at<N, INV>(ST);
+    static constexpr int RAD = radix_at<R, N, INV>(ST);
+    static constexpr int P = span_at<R, N, INV>(ST);
     static constexpr int NB = E / RAD;
     static constexpr int STRIDE = N / RAD;  // a multiple of 8 for every plan
 
@@ -226,7 +291,7 @@ template <class R, int N, bool INV, int ST> struct Stage {
         for (int m = 0; m < NB; ++m) {
             if constexpr (P > 1) {
                 const int k = (t + T * m) % P;
-                const cpx<R>* w = tws + tw_base<N, INV>() + tw_stage_offset<N, INV>(ST) + k * (RAD + 1);
+                const cpx<R>* w = tws + tw_base<R, N, INV>() + tw_stage_offset<R, N, INV>(ST) + k * (RAD + 1);
                 if constexpr (std::is_same<R, float>::value && RAD == 8) {
                     // FP32: w^2, w^3, w^5, w^6, w^7 from the loaded w and w^4 (two table reads
                     // instead of seven; a few ulps more twiddle error, far below FP32's bar)
@@ -279,17 +344,17 @@ template <class R, int N, bool INV, int ST> struct Stage {
 
 // Element index held in register slot j after the last stage of a transform (and the
 // input index of slot j for the first stage of the opposite-direction transform).
-template <int N, bool INV> SP_D int last_element(int t, int j)
+template <class R, int N, bool INV> SP_D int last_element(int t, int j)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
-    constexpr int RL = radix_at<N, INV>(FFTPlan<N>::NS - 1);
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int RL = radix_at<R, N, INV>(PlanOf<R, N>::NS - 1);
     return t + T * (j / RL) + (j % RL) * (N / RL);
 }
 // Element index of register slot j for the first stage of a transform.
-template <int N, bool INV> SP_D int first_element(int t, int j)
+template <class R, int N, bool INV> SP_D int first_element(int t, int j)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
-    constexpr int R0 = radix_at<N, INV>(0);
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int R0 = radix_at<R, N, INV>(0);
     return t + T * (j / R0) + (j % R0) * (N / R0);
 }
 
@@ -301,12 +366,12 @@ template <int N, bool INV> SP_D int first_element(int t, int j)
 // With other == fresh (one buffer) a second barrier follows each read.  Returns the
 // buffer that is safe to write after the call.  All threads of the block must call this.
 template <class R, int N, bool INV, int S, bool HALF0, class Lay, int ST = 0>
-SP_D cpx<R>* run_stages(cpx<R> (&v)[FFTPlan<N>::E], cpx<R>* fresh, cpx<R>* other, const Lay& lay,
+SP_D cpx<R>* run_stages(cpx<R> (&v)[PlanOf<R, N>::E], cpx<R>* fresh, cpx<R>* other, const Lay& lay,
                         const cpx<R>* tws, int t)
 {
     using St = Stage<R, N, INV, ST>;
     St::template compute<S, HALF0 && ST == 0>(v, tws, t);
-    if constexpr (ST + 1 < FFTPlan<N>::NS) {
+    if constexpr (ST + 1 < PlanOf<R, N>::NS) {
         St::store(v, fresh, lay, t);
         __syncthreads();
         Stage<R, N, INV, ST + 1>::load(v, fresh, lay, t);

@@ -58,7 +58,7 @@ template <int N> struct LayLine {
 // are read from global memory, below), then one or two exchange buffers (two when both
 // fit in 100 KB, for one barrier per stage).  The twiddle entry count is rounded up to
 // an even count, so that everything after it starts on a 16-byte boundary.
-template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<N>() + 1) & ~1; }
+template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<R, N>() + 1) & ~1; }
 // Passes whose staged twiddles come from global memory (the plan's copy after its N base
 // twiddles, cached in L1) rather than shared memory: double-float, whose tables (21 KB
 // per CTA at 512, 56 KB at 1024) limit the resident CTAs and cost a fill per CTA
@@ -97,7 +97,7 @@ template <int N> constexpr int lanes_b_default() { return N >= 1024 ? 4 : 8; }
 // Resident CTAs per SM requested from the compiler: 1024 threads per SM (at most 64
 // registers per thread) for the 8-value plans, to hide global-memory latency; the
 // 24-value plans (lengths with a factor 3) keep their registers.
-template <int N, int THREADS> constexpr int min_blocks() { return FFTPlan<N>::E <= 8 ? 1024 / THREADS : 1; }
+template <class R, int N, int THREADS> constexpr int min_blocks() { return PlanOf<R, N>::E <= 8 ? 1024 / THREADS : 1; }
 
 // LGB >= 0: the tile 2^LGB is a compile-time constant (the default tile); LGB = -1: the
 // tile comes from a.lgB (other tiles chosen by the autotuner).
@@ -107,16 +107,16 @@ template <class R, int N> constexpr int lg_max()
 }
 template <class R, int N, int LGB> constexpr int line_threads()
 {
-    return (N / FFTPlan<N>::E) << (LGB >= 0 ? LGB : lg_max<R, N>());
+    return (N / PlanOf<R, N>::E) << (LGB >= 0 ? LGB : lg_max<R, N>());
 }
 template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
 
 template <class R, int N, int MODE, int LGB>
-__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<N, line_threads<R, N, LGB>()>() : 1)
+__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<R, N, line_threads<R, N, LGB>()>() : 1)
     k2_line(LArgs a)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
-    constexpr int R0 = FFTPlan<N>::R[0];
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int R0 = PlanOf<R, N>::R[0];
     using Lay = LayStrided<R>;
     const int lgB = LGB >= 0 ? LGB : a.lgB, B = 1 << lgB;
     const int BUF = Lay::size(N, B);
@@ -141,13 +141,13 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
     if constexpr (MODE == INV) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = first_element<N, true>(t, j);
+            const int e = first_element<R, N, true>(t, j);
             v[j] = cv ? in[e * a.in_es] : czero<R>();
         }
     } else {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = first_element<N, false>(t, j);
+            const int e = first_element<R, N, false>(t, j);
             v[j] = (cv && (j % R0) < R0 / 2) ? in[e * a.in_es] : czero<R>();
         }
     }
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
         const long long mrow = (long long)ko * (a.nh_line + 1);
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = last_element<N, false>(t, j);
+            const int e = last_element<R, N, false>(t, j);
             const int ke = e <= N / 2 ? e : N - e;
             mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
         }
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             if constexpr (!PREFETCH_M) {
-                const int e = last_element<N, false>(t, j);
+                const int e = last_element<R, N, false>(t, j);
                 const int ke = e <= N / 2 ? e : N - e;
                 mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
             }
@@ -192,11 +192,11 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
     if constexpr (MODE == FWD) {
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if (cv) out[last_element<N, false>(t, j) * a.out_es] = norm(v[j]);
+            if (cv) out[last_element<R, N, false>(t, j) * a.out_es] = norm(v[j]);
     } else {  // the last inverse radix is R0: outputs q < R0/2 are the kept half
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
+            if ((j % R0) < R0 / 2 && cv) out[last_element<R, N, true>(t, j) * a.out_es] = norm(v[j]);
     }
 }
 
@@ -240,11 +240,11 @@ template <class R, int N, int MODE> constexpr size_t pipe_smem()
 }
 
 template <class R, int N, int MODE>
-__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blocks<N, line_threads<R, N, lg_default<N>()>()>())
+__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blocks<R, N, line_threads<R, N, lg_default<N>()>()>())
     k3_line(PArgs pa)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
-    constexpr int R0 = FFTPlan<N>::R[0];
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int R0 = PlanOf<R, N>::R[0];
     constexpr int LGB = lg_default<N>(), B = 1 << LGB;
     constexpr int NIN = stage_rows<R, N, MODE>();
     constexpr int CH = B * (int)sizeof(cpx<R>) / 16;  // 16-byte chunks per row
@@ -308,11 +308,11 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
         cpx<R> v[E];
         if constexpr (MODE == INV) {
 #pragma unroll
-            for (int j = 0; j < E; ++j) v[j] = stg[first_element<N, true>(t, j) * B + b];
+            for (int j = 0; j < E; ++j) v[j] = stg[first_element<R, N, true>(t, j) * B + b];
         } else {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                v[j] = ((j % R0) < R0 / 2) ? stg[first_element<N, false>(t, j) * B + b] : czero<R>();
+                v[j] = ((j % R0) < R0 / 2) ? stg[first_element<R, N, false>(t, j) * B + b] : czero<R>();
         }
         constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
         R mv[MODE == XMUL ? E : 1];
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
         if constexpr (PREFETCH_M) {
 #pragma unroll
             for (int j = 0; j < E; ++j) {
-                const int e = last_element<N, false>(t, j);
+                const int e = last_element<R, N, false>(t, j);
                 const int ke = e <= N / 2 ? e : N - e;
                 mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
             }
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 if constexpr (!PREFETCH_M) {
-                    const int e = last_element<N, false>(t, j);
+                    const int e = last_element<R, N, false>(t, j);
                     const int ke = e <= N / 2 ? e : N - e;
                     mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
                 }
@@ -351,11 +351,11 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blo
         if constexpr (MODE == FWD) {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                if (cv) out[last_element<N, false>(t, j) * a.out_es] = norm(v[j]);
+                if (cv) out[last_element<R, N, false>(t, j) * a.out_es] = norm(v[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                if ((j % R0) < R0 / 2 && cv) out[last_element<N, true>(t, j) * a.out_es] = norm(v[j]);
+                if ((j % R0) < R0 / 2 && cv) out[last_element<R, N, true>(t, j) * a.out_es] = norm(v[j]);
         }
         __syncthreads();  // exchange buffers free before the next tile's first write
         cur = nxt;
@@ -389,12 +389,12 @@ template <class R, int N> SP_HD bool z_two_buffers(int B)
 }
 
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
-                                  min_blocks<N, (N / FFTPlan<N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
+__global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
+                                  min_blocks<R, N, (N / PlanOf<R, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
     const int B = a.B;
-    constexpr int R0 = FFTPlan<N>::R[0];
+    constexpr int R0 = PlanOf<R, N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     cpx<R> v[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-        const int z = first_element<N, false>(t, j);
+        const int z = first_element<R, N, false>(t, j);
         R xr = Num<R>::c(0.0), xi = Num<R>::c(0.0);
         if ((j % R0) < R0 / 2) {  // z < n2: the padded half is zero
             if (l0 < a.lines) xr = to_r<R, Tio>(rho[l0 * n2 + z]);
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
     __syncthreads();
     cpx<R>* sm = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
 #pragma unroll
-    for (int j = 0; j < E; ++j) sm[lay(last_element<N, false>(t, j))] = v[j];
+    for (int j = 0; j < E; ++j) sm[lay(last_element<R, N, false>(t, j))] = v[j];
     __syncthreads();
     // two real lines from one complex transform: Xa = (Z_k + conj Z_{N-k}) / 2,
     // Xb = (Z_k - conj Z_{N-k}) / (2 i), k = 0..n2
@@ -436,12 +436,12 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
 }
 
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
-                                  min_blocks<N, (N / FFTPlan<N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
+__global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
+                                  min_blocks<R, N, (N / PlanOf<R, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
 {
-    constexpr int E = FFTPlan<N>::E, T = N / E;
+    constexpr int E = PlanOf<R, N>::E, T = N / E;
     const int B = a.B;
-    constexpr int R0 = FFTPlan<N>::R[0];
+    constexpr int R0 = PlanOf<R, N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__((N / FFTPlan<N>::E) * pairs_max<N>(),
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         if ((j % R0) < R0 / 2) {  // z < n2
-            const int z = last_element<N, true>(t, j);
+            const int z = last_element<R, N, true>(t, j);
             if (l0 < a.lines) u[l0 * n2 + z] = from_r<R, Tio>(re_of(v[j]));
             if (l1 < a.lines) u[l1 * n2 + z] = from_r<R, Tio>(im_of(v[j]));
         }
@@ -502,7 +502,7 @@ template <auto KERNEL> inline sp_status smem_attr(size_t bytes)
 template <class R, int N, int MODE>
 sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
 {
-    constexpr int E = FFTPlan<N>::E;
+    constexpr int E = PlanOf<R, N>::E;
     LArgs ab = a;
     ab.B = a.B ? a.B : lanes_b_default<N>();
     const int B = ab.B;
@@ -551,7 +551,7 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
 template <class R, class Tio, int N>
 sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
 {
-    constexpr int E = FFTPlan<N>::E;
+    constexpr int E = PlanOf<R, N>::E;
     ZArgs2 ab = a;
     ab.B = a.B ? a.B : pairs_default<N>();
     const int B = ab.B;
@@ -587,7 +587,7 @@ template <class R> struct StageTw {
     template <int N> sp_status run()
     {
         if constexpr (tw_global<R, N>()) {
-            static_assert(tw_stage_size<N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
+            static_assert(tw_stage_size<R, N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
             k_stage_twiddles<R, N><<<16, 256, 0, st>>>(tw + N, tw);
             return sp_cuda_check(cudaGetLastError(), "staged twiddles");
         }
