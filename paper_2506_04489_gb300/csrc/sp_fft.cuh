@@ -89,7 +89,14 @@ struct Plan256Radix16 {
     static constexpr int NS = 2, E = 16;
     static constexpr int R[2] = {16, 16};
 };
+// At 512, FP32 takes radices 32-16 (32 values a thread, one exchange instead of two:
+// the x pass 19 % faster, the z passes slower, the 256^3 solve 9 % faster).
+struct Plan512Radix32 {
+    static constexpr int NS = 2, E = 32;
+    static constexpr int R[2] = {32, 16};
+};
 template <class R, int N> struct PlanOf : FFTPlan<N> {};
+template <> struct PlanOf<float, 512> : Plan512Radix32 {};
 template <> struct PlanOf<float, 256> : Plan256Radix16 {};
 template <> struct PlanOf<float, 1024> : Plan1024Radix16 {};
 template <> struct PlanOf<double, 1024> : Plan1024Radix16 {};
@@ -221,9 +228,68 @@ template <int S, class R> SP_D void bf16_half(cpx<R>* u)
     bf16_tail<S>(u, e, o);
 }
 
+// radix 32 as 2 x 16: X_q = E_q + w^q O_q, X_{q+16} = E_q - w^q O_q, w = exp(S 2 pi i / 32).
+template <int S, class R> SP_D void bf32_tail(cpx<R>* u, cpx<R>* e, cpx<R>* o)
+{
+    // cos and sin of pi m / 16, m = 0..8
+    constexpr double C[9] = {1.0, 0.980785280403230449126182236134239037, 0.923879532511286756128183189396788287,
+                             0.831469612302545237078788377617905757, 0.707106781186547524400844362104849039,
+                             0.555570233019602224742830813948532874, 0.382683432365089771728459984030398867,
+                             0.195090322016128267848284868477022241, 0.0};
+    constexpr double Sn[9] = {0.0, 0.195090322016128267848284868477022241, 0.382683432365089771728459984030398867,
+                              0.555570233019602224742830813948532874, 0.707106781186547524400844362104849039,
+                              0.831469612302545237078788377617905757, 0.923879532511286756128183189396788287,
+                              0.980785280403230449126182236134239037, 1.0};
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        cpx<R> t;
+        if (q == 0) {
+            t = o[0];
+        } else if (q == 8) {
+            t = mul_si<S>(o[8]);
+        } else {
+            const double c = q < 8 ? C[q] : -C[16 - q];
+            const double sn = q < 8 ? Sn[q] : Sn[16 - q];
+            t = tw_mul(o[q], mk(Num<R>::c(c), Num<R>::c(S > 0 ? sn : -sn)));
+        }
+        u[q] = e[q] + t;
+        u[q + 16] = e[q] - t;
+    }
+}
+
+template <int S, class R> SP_D void bf32(cpx<R>* u)
+{
+    cpx<R> e[16], o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        e[j] = u[2 * j];
+        o[j] = u[2 * j + 1];
+    }
+    bf16<S>(e);
+    bf16<S>(o);
+    bf32_tail<S>(u, e, o);
+}
+
+// radix 32 with u[16..31] = 0
+template <int S, class R> SP_D void bf32_half(cpx<R>* u)
+{
+    cpx<R> e[16], o[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        e[j] = u[2 * j];
+        o[j] = u[2 * j + 1];
+    }
+    bf16_half<S>(e);
+    bf16_half<S>(o);
+    bf32_tail<S>(u, e, o);
+}
+
 template <int RAD, int S, bool HALF, class R> SP_D void butterfly(cpx<R>* u)
 {
-    if constexpr (RAD == 16) {
+    if constexpr (RAD == 32) {
+        if constexpr (HALF) bf32_half<S>(u);
+        else bf32<S>(u);
+    } else if constexpr (RAD == 16) {
         if constexpr (HALF) bf16_half<S>(u);
         else bf16<S>(u);
     } else if constexpr (RAD == 8) {
