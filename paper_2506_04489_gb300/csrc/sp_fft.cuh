@@ -101,6 +101,12 @@ template <> struct PlanOf<float, 256> : Plan256Radix16 {};
 template <> struct PlanOf<float, 1024> : Plan1024Radix16 {};
 template <> struct PlanOf<double, 1024> : Plan1024Radix16 {};
 template <> struct PlanOf<df32, 384> : Plan384Radix4 {};
+// Plan key of the z passes (contiguous real lines, packed in pairs): the type's own plan,
+// except FP32 at 512, whose z passes run faster on 8-8-8 than on the 32-16 plan of its
+// line passes.  Each axis has its own staged twiddle table, so the z axis can differ.
+template <class R> struct ZKey {};
+template <class R, int N> struct PlanOf<ZKey<R>, N> : PlanOf<R, N> {};
+template <> struct PlanOf<ZKey<float>, 512> : FFTPlan<512> {};
 
 // radix of stage s of the forward (INV = false) or inverse (reversed) transform
 template <class R, int N, bool INV> constexpr int radix_at(int s)
@@ -327,29 +333,29 @@ template <class R, int N> constexpr int tw_stage_size()
 }
 template <class R, int N, bool INV> constexpr int tw_base() { return INV ? tw_stage_offset<R, N, false>(PlanOf<R, N>::NS) : 0; }
 
-// Fill the staged tables (all threads of the block; a barrier must follow).
-template <class R, int N, bool INV, int ST = 0>
+// Fill the staged tables of plan key K (all threads of the block; a barrier must follow).
+template <class R, int N, bool INV, class K = R, int ST = 0>
 SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int tid, int nthreads)
 {
-    if constexpr (ST < PlanOf<R, N>::NS) {
-        constexpr int P = span_at<R, N, INV>(ST), RAD = radix_at<R, N, INV>(ST);
+    if constexpr (ST < PlanOf<K, N>::NS) {
+        constexpr int P = span_at<K, N, INV>(ST), RAD = radix_at<K, N, INV>(ST);
         if constexpr (P > 1) {
             constexpr int TWS = N / (P * RAD);
-            cpx<R>* dst = tws + tw_base<R, N, INV>() + tw_stage_offset<R, N, INV>(ST);
+            cpx<R>* dst = tws + tw_base<K, N, INV>() + tw_stage_offset<K, N, INV>(ST);
             for (int j = tid; j < P * RAD; j += nthreads) {
                 const int k = j / RAD, r = j % RAD;
                 dst[k * (RAD + 1) + r] = tw[r * k * TWS];
             }
         }
-        fill_stage_twiddles<R, N, INV, ST + 1>(tws, tw, tid, nthreads);
+        fill_stage_twiddles<R, N, INV, K, ST + 1>(tws, tw, tid, nthreads);
     }
 }
 
-template <class R, int N, bool INV, int ST> struct Stage {
-    static constexpr int E = PlanOf<R, N>::E;
+template <class R, int N, bool INV, int ST, class K = R> struct Stage {
+    static constexpr int E = PlanOf<K, N>::E;
     static constexpr int T = N / E;
-    static constexpr int RAD = radix_at<R, N, INV>(ST);
-    static constexpr int P = span_at<R, N, INV>(ST);
+    static constexpr int RAD = radix_at<K, N, INV>(ST);
+    static constexpr int P = span_at<K, N, INV>(ST);
     static constexpr int NB = E / RAD;
     static constexpr int STRIDE = N / RAD;  // a multiple of 8 for every plan
 
@@ -372,7 +378,7 @@ template <class R, int N, bool INV, int ST> struct Stage {
         for (int m = 0; m < NB; ++m) {
             if constexpr (P > 1) {
                 const int k = (t + T * m) % P;
-                const cpx<R>* w = tws + tw_base<R, N, INV>() + tw_stage_offset<R, N, INV>(ST) + k * (RAD + 1);
+                const cpx<R>* w = tws + tw_base<K, N, INV>() + tw_stage_offset<K, N, INV>(ST) + k * (RAD + 1);
                 if constexpr (std::is_same<R, float>::value && RAD == 8) {
                     // FP32: w^2, w^3, w^5, w^6, w^7 from the loaded w and w^4 (two table reads
                     // instead of seven; a few ulps more twiddle error, far below FP32's bar)
@@ -446,18 +452,18 @@ template <class R, int N, bool INV> SP_D int first_element(int t, int j)
 // each: a buffer is written again only after the barrier that follows every read of it.
 // With other == fresh (one buffer) a second barrier follows each read.  Returns the
 // buffer that is safe to write after the call.  All threads of the block must call this.
-template <class R, int N, bool INV, int S, bool HALF0, class Lay, int ST = 0>
-SP_D cpx<R>* run_stages(cpx<R> (&v)[PlanOf<R, N>::E], cpx<R>* fresh, cpx<R>* other, const Lay& lay,
+template <class R, int N, bool INV, int S, bool HALF0, class K = R, class Lay, int ST = 0>
+SP_D cpx<R>* run_stages(cpx<R> (&v)[PlanOf<K, N>::E], cpx<R>* fresh, cpx<R>* other, const Lay& lay,
                         const cpx<R>* tws, int t)
 {
-    using St = Stage<R, N, INV, ST>;
+    using St = Stage<R, N, INV, ST, K>;
     St::template compute<S, HALF0 && ST == 0>(v, tws, t);
-    if constexpr (ST + 1 < PlanOf<R, N>::NS) {
+    if constexpr (ST + 1 < PlanOf<K, N>::NS) {
         St::store(v, fresh, lay, t);
         __syncthreads();
-        Stage<R, N, INV, ST + 1>::load(v, fresh, lay, t);
+        Stage<R, N, INV, ST + 1, K>::load(v, fresh, lay, t);
         if (other == fresh) __syncthreads();
-        return run_stages<R, N, INV, S, HALF0, Lay, ST + 1>(v, other, fresh, lay, tws, t);
+        return run_stages<R, N, INV, S, HALF0, K, Lay, ST + 1>(v, other, fresh, lay, tws, t);
     } else {
         return fresh;
     }

@@ -65,7 +65,7 @@ template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<R, 
 // (measured: 8 % faster at 128^3, 5 % at 256^3, 17 % at 512^3), and FP32 (its z passes
 // 20-30 % faster).  The pipelined line kernel keeps its tables in shared memory.
 template <class R, int N> constexpr bool tw_global() { return std::is_same<R, df32>::value || std::is_same<R, float>::value; }
-template <class R, int N> constexpr size_t pass_tw_bytes() { return tw_global<R, N>() ? 0 : sizeof(cpx<R>) * tw_entries<R, N>(); }
+template <class R, int N, class K = R> constexpr size_t pass_tw_bytes() { return tw_global<R, N>() ? 0 : sizeof(cpx<R>) * tw_entries<K, N>(); }
 constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 
 // ------------------------------------------------------------------ strided passes
@@ -385,23 +385,23 @@ SP_D long long w_row(const ZArgs2& a, long long l) { return (l / a.n1) * a.plane
 template <class R, int N> SP_HD int z_buf(int B) { return B * LayLine<N>::LD; }
 template <class R, int N> SP_HD bool z_two_buffers(int B)
 {
-    return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), pass_tw_bytes<R, N>());
+    return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), pass_tw_bytes<R, N, ZKey<R>>());
 }
 
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
-                                  min_blocks<R, N, (N / PlanOf<R, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
+__global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
+                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
 {
-    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int E = PlanOf<ZKey<R>, N>::E, T = N / E;
     const int B = a.B;
-    constexpr int R0 = PlanOf<R, N>::R[0];
+    constexpr int R0 = PlanOf<ZKey<R>, N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N, ZKey<R>>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
     const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
-    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, false>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
+    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, false, ZKey<R>>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     const Tio* rho = static_cast<const Tio*>(a.rho) + blockIdx.y * a.io_bs;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
     cpx<R> v[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-        const int z = first_element<R, N, false>(t, j);
+        const int z = first_element<ZKey<R>, N, false>(t, j);
         R xr = Num<R>::c(0.0), xi = Num<R>::c(0.0);
         if ((j % R0) < R0 / 2) {  // z < n2: the padded half is zero
             if (l0 < a.lines) xr = to_r<R, Tio>(rho[l0 * n2 + z]);
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
         v[j] = mk(xr, xi);
     }
     __syncthreads();
-    cpx<R>* sm = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
+    cpx<R>* sm = run_stages<R, N, false, -1, true, ZKey<R>>(v, sm0, sm1, lay, tws, t);
 #pragma unroll
-    for (int j = 0; j < E; ++j) sm[lay(last_element<R, N, false>(t, j))] = v[j];
+    for (int j = 0; j < E; ++j) sm[lay(last_element<ZKey<R>, N, false>(t, j))] = v[j];
     __syncthreads();
     // two real lines from one complex transform: Xa = (Z_k + conj Z_{N-k}) / 2,
     // Xb = (Z_k - conj Z_{N-k}) / (2 i), k = 0..n2
@@ -436,19 +436,19 @@ __global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
 }
 
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
-                                  min_blocks<R, N, (N / PlanOf<R, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
+__global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
+                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
 {
-    constexpr int E = PlanOf<R, N>::E, T = N / E;
+    constexpr int E = PlanOf<ZKey<R>, N>::E, T = N / E;
     const int B = a.B;
-    constexpr int R0 = PlanOf<R, N>::R[0];
+    constexpr int R0 = PlanOf<ZKey<R>, N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N, ZKey<R>>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
     const int tid = threadIdx.x, b = tid / T, t = tid % T;
     const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
-    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, true>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
+    if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, true, ZKey<R>>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
     const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
     Tio* u = static_cast<Tio*>(a.u) + blockIdx.y * a.io_bs;
@@ -467,13 +467,13 @@ __global__ void __launch_bounds__((N / PlanOf<R, N>::E) * pairs_max<N>(),
     }
     __syncthreads();
     cpx<R> v[E];
-    Stage<R, N, true, 0>::load(v, sm0, lay, t);
+    Stage<R, N, true, 0, ZKey<R>>::load(v, sm0, lay, t);
     if (sm1 == sm0) __syncthreads();
-    run_stages<R, N, true, +1, false>(v, sm1, sm0, lay, tws, t);
+    run_stages<R, N, true, +1, false, ZKey<R>>(v, sm1, sm0, lay, tws, t);
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         if ((j % R0) < R0 / 2) {  // z < n2
-            const int z = last_element<R, N, true>(t, j);
+            const int z = last_element<ZKey<R>, N, true>(t, j);
             if (l0 < a.lines) u[l0 * n2 + z] = from_r<R, Tio>(re_of(v[j]));
             if (l1 < a.lines) u[l1 * n2 + z] = from_r<R, Tio>(im_of(v[j]));
         }
@@ -551,12 +551,12 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
 template <class R, class Tio, int N>
 sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
 {
-    constexpr int E = PlanOf<R, N>::E;
+    constexpr int E = PlanOf<ZKey<R>, N>::E;
     ZArgs2 ab = a;
     ab.B = a.B ? a.B : pairs_default<N>();
     const int B = ab.B;
     if (B < 1 || B > pairs_max<N>() || (pairs_max<N>() % B)) return sp_fail(SP_ERR_INVALID, "bad z tile %d", B);
-    const size_t smem = pass_tw_bytes<R, N>() + sizeof(cpx<R>) * (z_two_buffers<R, N>(B) ? 2 : 1) * z_buf<R, N>(B);
+    const size_t smem = pass_tw_bytes<R, N, ZKey<R>>() + sizeof(cpx<R>) * (z_two_buffers<R, N>(B) ? 2 : 1) * z_buf<R, N>(B);
     const long long pairs = (a.lines + 1) / 2;
     dim3 grid((unsigned)((pairs + B - 1) / B), (unsigned)batch);
     sp_status rc;
@@ -571,24 +571,26 @@ sp_status launch_z(const ZArgs2& a, bool forward, int batch, cudaStream_t st)
 }
 
 // Length dispatch: calls f.template run<N>() for a supported N.
-template <class R, int N>
+template <class R, int N, class K>
 __global__ void k_stage_twiddles(cpx<R>* dst, const cpx<R>* __restrict__ tw)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    fill_stage_twiddles<R, N, false>(dst, tw, tid, nth);
-    fill_stage_twiddles<R, N, true>(dst, tw, tid, nth);
+    fill_stage_twiddles<R, N, false, K>(dst, tw, tid, nth);
+    fill_stage_twiddles<R, N, true, K>(dst, tw, tid, nth);
 }
 
 template <class F> inline sp_status with_len(int N, F&& f);
 
-template <class R> struct StageTw {
+// K: the plan key of the passes that read the table (R for the line passes, ZKey<R> for
+// the z passes).
+template <class R, class K> struct StageTw {
     cpx<R>* tw;
     cudaStream_t st;
     template <int N> sp_status run()
     {
         if constexpr (tw_global<R, N>()) {
-            static_assert(tw_stage_size<R, N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
-            k_stage_twiddles<R, N><<<16, 256, 0, st>>>(tw + N, tw);
+            static_assert(tw_stage_size<K, N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
+            k_stage_twiddles<R, N, K><<<16, 256, 0, st>>>(tw + N, tw);
             return sp_cuda_check(cudaGetLastError(), "staged twiddles");
         }
         return SP_OK;
@@ -640,7 +642,8 @@ template <class R> sp_status stage_twiddles(sp_plan p, cudaStream_t st)
 {
     for (int ax = 0; ax < 3; ++ax) {
         if (!len_ok(p->N[ax])) continue;
-        sp_status rc = with_len(p->N[ax], StageTw<R>{static_cast<cpx<R>*>(const_cast<void*>(Tabs<R>::tw(p, ax))), st});
+        cpx<R>* tw = static_cast<cpx<R>*>(const_cast<void*>(Tabs<R>::tw(p, ax)));
+        sp_status rc = ax == 2 ? with_len(p->N[ax], StageTw<R, ZKey<R>>{tw, st}) : with_len(p->N[ax], StageTw<R, R>{tw, st});
         if (rc) return rc;
     }
     return SP_OK;
