@@ -224,12 +224,20 @@ struct PArgs {
 template <class R, int N, int MODE> constexpr int stage_rows() { return MODE == INV ? N : N / 2; }
 // Two exchange buffers when they fit beside the twiddles and the stage in 110 KB (two CTAs
 // per SM), else one.
+// The y passes of the 32-value plan at 512 (one exchange a transform) trade the second
+// buffer for a third resident CTA (measured: y passes 10 % faster; the x pass, with two
+// transforms a tile, and the 1024 passes are faster with two buffers and two CTAs).
+template <class R, int N, int MODE> constexpr bool pipe_third_cta()
+{
+    return PlanOf<R, N>::E >= 32 && MODE != XMUL && N <= 512;
+}
 template <class R, int N, int MODE> constexpr bool pipe_two_buffers()
 {
     constexpr int B = 1 << lg_default<N>();
     constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
     constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
-    return twb + 2 * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B <= 110 * 1024;
+    return !pipe_third_cta<R, N, MODE>() &&
+           twb + 2 * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B <= 110 * 1024;
 }
 template <class R, int N, int MODE> constexpr size_t pipe_smem()
 {
@@ -240,7 +248,8 @@ template <class R, int N, int MODE> constexpr size_t pipe_smem()
 }
 
 template <class R, int N, int MODE>
-__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(), min_blocks<R, N, line_threads<R, N, lg_default<N>()>()>())
+__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(),
+                                  pipe_third_cta<R, N, MODE>() ? 3 : min_blocks<R, N, line_threads<R, N, lg_default<N>()>()>())
     k3_line(PArgs pa)
 {
     constexpr int E = PlanOf<R, N>::E, T = N / E;
