@@ -359,7 +359,22 @@ SP_D void fill_stage_twiddles(cpx<R>* tws, const cpx<R>* __restrict__ tw, int ti
     }
 }
 
+// A plan is usable when its radices multiply to N, every radix divides E (each thread
+// runs whole butterflies) and every stage stride N / radix is a multiple of 8 (the
+// layouts' step rule).
+template <class K, int N> constexpr bool plan_ok()
+{
+    int prod = 1;
+    for (int i = 0; i < PlanOf<K, N>::NS; ++i) {
+        const int r = PlanOf<K, N>::R[i];
+        if (PlanOf<K, N>::E % r != 0 || (N / r) % 8 != 0) return false;
+        prod *= r;
+    }
+    return prod == N;
+}
+
 template <class R, int N, bool INV, int ST, class K = R> struct Stage {
+    static_assert(plan_ok<K, N>(), "radix plan does not fit the stage rules");
     static constexpr int E = PlanOf<K, N>::E;
     static constexpr int T = N / E;
     static constexpr int RAD = radix_at<K, N, INV>(ST);
