@@ -37,7 +37,18 @@ sys.path.insert(0, ROOT)
 
 N_GRID = 256
 BOX = (-1.0, 1.0)
-ORACLE_SAMPLE_N = 128
+# the headline metric, printed identically by both arms
+METRIC = "grid pts/s at 256\u00b3 (FP64 1e-12 vs FP32 1e-5), % HBM roofline; served p50/p99"
+
+
+def workload_config(n, world=1):
+    """The workload both arms time: one solve (Alg. 2) of the bump density on [-1,1]^3."""
+    return {"workload": f"bump exp(-1/(1-r^2/0.64)) density on [-1,1]^3, {n}^3 grid, padded {2 * n}^3, "
+                        f"solve phase (Alg. 2), one independent solve per GPU",
+            "grid": n, "box": list(BOX), "precision": "FP64 in/out at the 1e-12 bar",
+            "l2": "inputs larger than L2: 3 rotating rho/u pairs of "
+                  f"{8 * n ** 3 / 1e6:.0f} MB plus the workspace",
+            "parallelism": f"replicas x{world}"}
 
 
 def parse():
@@ -46,10 +57,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--grid", type=int, default=N_GRID, help="grid points per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration legs")
     ap.add_argument("--profile", nargs=3, metavar=("N", "PRECISION", "SOLVES"),
                     help="only build one plan and run SOLVES solves (a small target for ncu)")
@@ -291,15 +302,37 @@ def max_over_ranks(x, world):
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_sample(steps=1, warmup=0):
-    """The FP64 CPU oracle on a bounded sample: 128^3 solves of the same density and box
-    (solve phase only; its own tables built first, untimed), all host threads."""
-    import numpy as np
+def host_cpu():
+    """Model name and logical core count of the host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model, "logical_cpus": os.cpu_count()}
 
+
+def oracle_solves(n, steps=1, warmup=0):
+    """The FP64 CPU oracle (Alg. 2, its own FFT, the full (2n)^3 padded grid) on the bump
+    density at n^3 on [-1,1]^3, all host threads: `warmup` untimed solves, then `steps`
+    timed ones (solve phase only; its tables are built first, untimed, as the paper's
+    timings exclude the precompute)."""
     import oracle
     from paper_2506_04489_gb300 import workloads as W
     oracle.set_threads(os.cpu_count() or 1)
-    n = ORACLE_SAMPLE_N
     _, _, M = oracle.plan_tables(n, *BOX)
     rho = W.bump_profile(n, *BOX)
     for _ in range(warmup):
@@ -310,21 +343,24 @@ def oracle_sample(steps=1, warmup=0):
         oracle.solve(M, rho)
         times.append(time.perf_counter() - t0)
     mean = sum(times) / len(times)
+    cpu = host_cpu()
     return {"value": n ** 3 / mean, "unit": "grid pts/s", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{steps} oracle solves of the bump density at {n}^3 on [-1,1]^3 (1/8 of the {N_GRID}^3 "
-                      f"workload's points; solve phase only, tables built first), mean {mean:.2f} s"}, mean
+            "cpu_model": cpu["model"], "logical_cpus": cpu["logical_cpus"],
+            "sample": f"{steps} full oracle solves of the bump density at {n}^3 on [-1,1]^3 (the benchmark "
+                      f"workload itself; solve phase only, tables built first), mean {mean:.2f} s"}, mean
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle itself on the benchmark workload (the paper
+    gives no implementation to run), one full 256^3 solve per step on the host cores."""
     if rank != 0:
         return 0
-    cpu, mean = oracle_sample(steps=args.steps, warmup=args.warmup)
-    line = {"impl": "reference", "metric": f"grid pts/s at {N_GRID}^3 (FP64 oracle on host cores, bounded sample)",
+    cpu, mean = oracle_solves(args.grid, steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC,
             "value": cpu["value"], "unit": "grid pts/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"bump exp(-1/(1-r^2/0.64)) on [-1,1]^3, {ORACLE_SAMPLE_N}^3 sample of the "
-                                   f"{N_GRID}^3 solve, FP64", "grid": ORACLE_SAMPLE_N},
+            "config": workload_config(args.grid, args.gpus),
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": "grid pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -332,14 +368,20 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def time_solves(plan, rhos, outs, steps, warmup, world, stream):
+def time_solves(plan, rhos, outs, steps, warmup, world, stream, instrument=False):
+    """W untimed solves, then K solves between CUDA events on `stream` (barrier and device
+    synchronise on both sides), max over ranks.  With `instrument`, every solve also
+    records an event between its passes (events created before the timed region), and
+    the per-pass totals are returned; the headline region runs without them."""
     import torch
+    if instrument:
+        plan.set_timing(True, reserve=max(steps, warmup, 1))
     for i in range(warmup):
         plan.solve(rhos[i % len(rhos)], outs[i % len(outs)], stream)
     barrier(world)
     torch.cuda.synchronize()
-    plan.pass_times()  # drop anything recorded before the timed region
-    plan.set_timing(True)
+    if instrument:
+        plan.pass_times()  # drop the warm-up record (its events return to the pool)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
@@ -348,9 +390,12 @@ def time_solves(plan, rhos, outs, steps, warmup, world, stream):
     end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    plan.set_timing(False)
     ms = start.elapsed_time(end)
-    return max_over_ranks(ms, world), plan.pass_times()
+    passes = None
+    if instrument:
+        passes = plan.pass_times()
+        plan.set_timing(False)
+    return max_over_ranks(ms, world), passes
 
 
 # FP32 pipe of the chip: 152 SMs x 128 FP32 lanes, one operation per lane per clock
@@ -358,7 +403,13 @@ def time_solves(plan, rhos, outs, steps, warmup, world, stream):
 FP32_LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
-def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
+def roofline_for(prec, n, passes, solve_ms, hbm_peak, peak_kind):
+    """Roofline of the dominant pass: its algorithmic bytes per launch (pass_model) over its
+    average launch duration (CUDA events between the passes of an instrumented timed
+    region) against the measured HBM bandwidth, for every precision.  Beside it: what
+    actually bounds the pass (FP32 pipe for double-float, FP64 pipe for native FP64: the
+    executed FP32 lane operations from ncu over the same duration, labelled as executed
+    work) and the whole solve's fraction on the minimal three-pass byte count."""
     model = pass_model(n, prec)
     name = max(passes, key=lambda k: passes[k][0])
     tot_ms, launches = passes[name]
@@ -366,38 +417,25 @@ def roofline_for(prec, n, passes, steps, hbm_peak, peak_kind):
     nbytes, nflops = model[name]
     workload = f"n{n}_{prec}"
     traffic = ncu_count(name, workload, "dram_bytes")
-    if prec == "fp64":
-        achieved = nflops / avg_s / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); HBM view in hbm_roofline",
-                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
-                "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
-    elif prec == "df32":
-        # double-float arithmetic runs on the FP32 pipe: the operations one launch executes
-        # (ncu instruction counts of this kernel on this workload, f32x2 forms twice) over
-        # its live average duration, against the pipe's one-per-lane-per-clock ceiling
+    achieved = nbytes / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": traffic, "avg_launch_ms": avg_s * 1e3, "algorithmic_bytes": nbytes,
+            "algorithmic_flops": nflops,
+            "solve_frac": minimal_bytes_per_point(prec) * n ** 3 / (solve_ms / 1e3) / 1e9 / hbm_peak,
+            "solve_frac_note": "minimal three-pass bytes per output point x n^3 / solve time / measured HBM"}
+    if prec == "df32":
         ops = ncu_count(name, workload, "fp32_lane_ops")
-        achieved = ops / avg_s / 1e12 if ops else None
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "unit": "T FP32 lane-ops/s",
-                "peak": FP32_LANE_PEAK_TOPS, "frac": achieved / FP32_LANE_PEAK_TOPS if ops else None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts and maximum clock; an FMA "
-                               "counts once)",
-                "ops_per_launch": ops,
-                "ops_source": "ncu FP32 instruction counts (fadd, fmul, ffma; f32x2 forms twice) of this "
-                              "kernel on this workload, profiles/ncu_counts.txt" if ops else
-                              "not captured for the current kernel sources",
-                "fp64_class": {"achieved": nflops / avg_s / 1e12, "unit": "TFLOP/s (5 N log2 N convention)",
-                               "vs_nominal_fp64_peak": nflops / avg_s / 1e12 / FP64_PEAK_TFLOPS},
-                "hbm_gbs": nbytes / avg_s / 1e9, "hbm_frac": nbytes / avg_s / 1e9 / hbm_peak,
-                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
-                "algorithmic_flops": nflops, "algorithmic_bytes": nbytes}
-    else:
-        achieved = nbytes / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
-                "algorithmic_bytes": nbytes}
+        roof["limiter"] = "FP32 pipe (double-float arithmetic)"
+        roof["fp32_issue_frac"] = ops / avg_s / 1e12 / FP32_LANE_PEAK_TOPS if ops else None
+        roof["fp32_issue_note"] = ("EXECUTED FP32 lane operations of this kernel (ncu fadd/fmul/ffma, f32x2 forms "
+                                   "twice, profiles/ncu_counts.txt) / avg launch / 152 SMs x 128 lanes x 2.07 GHz; "
+                                   "executed work, not the method's")
+        roof["fp64_class_tflops"] = nflops / avg_s / 1e12
+    elif prec == "fp64":
+        roof["limiter"] = "FP64 pipe"
+        roof["fp64_pipe_frac"] = nflops / avg_s / 1e12 / FP64_PEAK_TFLOPS
+        roof["fp64_pipe_note"] = "algorithmic flops (5 N log2 N per line) / avg launch / nominal 1.25 TFLOP/s"
     share = {k: round(v[0] / sum(x[0] for x in passes.values()), 4) for k, v in passes.items()}
     roof["pass_share"] = share
     return roof
@@ -407,8 +445,8 @@ def run_served(args):
     """Served stream: Poisson arrivals (mean 200/s, seed 0) of solves with n drawn from
     {32, 64, 96, 128, 192, 256} and accuracy from {1e-6 (FP32), 1e-12 (double-float)}, bump
     densities, device-resident plans (built before traffic) under a 120 GB budget; p50/p99
-    latency and solves/s over the requests arriving after a 2 s warm-up; results go to
-    pinned buffers the client owns and reuses."""
+    latency and solves/s over the requests arriving in 30 s after a 2 s warm-up; results go
+    to pinned buffers the client owns and reuses."""
     import torch
 
     from paper_2506_04489_gb300 import serve, workloads as W
@@ -594,7 +632,7 @@ def run_ours(args, world, rank, local):
     from paper_2506_04489_gb300 import Plan, workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.n
+    n = args.grid
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
     rho_np = W.bump_profile(n, *BOX)
@@ -611,12 +649,17 @@ def run_ours(args, world, rank, local):
         base = torch.from_numpy(rho_np).to(dev, dtype=dt)
         rhos = [base.clone() for _ in range(3)]
         outs = [torch.empty_like(base) for _ in range(3)]
-        ms, passes = time_solves(plan, rhos, outs, args.steps, args.warmup, world, stream)
+        # the headline region: plain solves, nothing recorded between the passes
+        ms, _ = time_solves(plan, rhos, outs, args.steps, args.warmup, world, stream)
         if prec == "df32":
             clocks = sampler.stop()
         ms_step = ms / args.steps
         value = world * n ** 3 / (ms_step / 1e3)
-        roof = roofline_for(prec, n, passes, args.steps, hbm_peak, peak_kind)
+        # a second timed region of the same K solves with an event between passes (events
+        # created beforehand): per-pass durations for the roofline of the dominant pass
+        ms_i, passes = time_solves(plan, rhos, outs, args.steps, 2, world, stream, instrument=True)
+        roof = roofline_for(prec, n, passes, ms_step, hbm_peak, peak_kind)
+        roof["instrumented_ms_per_step"] = ms_i / args.steps
         hbm_frac = minimal_bytes_per_point(prec) * n ** 3 / (ms_step / 1e3) / 1e9 / hbm_peak
         launches = sum(v[1] for v in passes.values())
         # live accuracy guard: deviation of this path from the native FP64 solve of the
@@ -634,8 +677,9 @@ def run_ours(args, world, rank, local):
                                           "peak_gbs": hbm_peak, "note": "bytes of the minimal 3-pass schedule / "
                                           "solve time / measured HBM bandwidth"},
                          "gpu_launches": launches}
-        # end to end through the public API: pinned host densities -> device -> solve ->
-        # pinned host potentials, each step's copies overlapped with its neighbours' solves
+        # end to end through the C ABI's host-buffer entry (sp_solve_host): pinned host
+        # densities -> device -> solve -> pinned host potentials, each step's copies
+        # overlapped with its neighbours' solves
         if prec == "df32":
             e2e_steps = max(10, args.steps)
             host_in = [torch.from_numpy(rho_np).to(dtype=dt).pin_memory() for _ in range(2)]
@@ -669,21 +713,16 @@ def run_ours(args, world, rank, local):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu, _ = oracle_sample(steps=2, warmup=0)
+        cpu, _ = oracle_solves(n, steps=2, warmup=0)
     r64 = results["df32"]
     line = {
-        "metric": f"grid pts/s at {n}^3 (FP64 1e-12 vs FP32 1e-5), % HBM roofline",
+        "metric": METRIC,
         "value": r64["value"], "unit": "grid pts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32x2 (double-float)", "data": "synthetic",
         "accuracy_path": "double-float passes (hi+lo FP32 pairs) meet the FP64 bar: oracle parity <= 1e-12 "
                          "in tests/; live max deviation from the native FP64 solve reported below",
-        "config": {"workload": f"bump exp(-1/(1-r^2/0.64)) density on [-1,1]^3, {n}^3 grid, padded {2 * n}^3, "
-                               f"solve phase (Alg. 2), one independent solve per GPU",
-                   "grid": n, "box": list(BOX), "precision": "df32 (FP64 in/out)",
-                   "l2": "inputs larger than L2: 3 rotating rho/u pairs of "
-                         f"{8 * n ** 3 / 1e6:.0f} MB plus the workspace",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(n, world),
         "roofline": r64["roofline"],
         "hbm_roofline": r64["hbm_roofline"],
         "max_rel_dev_from_fp64": r64["max_rel_dev_from_fp64"],

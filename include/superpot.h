@@ -92,6 +92,35 @@ sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
                          int max_batch);
 
 /*
+ * sp_allocator -- where a plan's device memory comes from (the multiplier, twiddles, 1D
+ * tables, GS table, status word and workspace; Alg. 1 storage and the solve workspace).
+ *   alloc   : returns `bytes` of device memory of `device` (the current device during the
+ *             call), aligned to at least 256 bytes, or NULL on failure (the plan then
+ *             fails with SP_ERR_OOM).  Called only from sp_plan_create_ex.
+ *   release : gives back a block that alloc returned, with the same size and device.
+ *             Called only from sp_plan_destroy (and from sp_plan_create_ex when it fails),
+ *             after the plan's work has completed, with `device` current.
+ *   ctx     : passed through to both.
+ * A framework with its own device pool (for example PyTorch's caching allocator) passes
+ * its allocation functions here so that plans draw on that pool.  The transient scratch
+ * of sp_kernel_precompute is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+ * precompute stream) in either case.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, int device, void* ctx);
+    void (*release)(void* ptr, size_t bytes, int device, void* ctx);
+    void* ctx;
+} sp_allocator;
+
+/* sp_plan_create_ex -- sp_plan_create with the plan's device memory taken from
+ * `allocator` (NULL: cudaMalloc/cudaFree, exactly sp_plan_create).  Both callbacks must
+ * be non-NULL when allocator is given (else SP_ERR_INVALID). */
+sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const double box_lo[3],
+                            const double box_hi[3], int padding, const double* gs_w,
+                            const double* gs_a, int gs_terms, double eps, sp_precision prec,
+                            int max_batch, const sp_allocator* allocator);
+
+/*
  * sp_plan_set_kernel -- which convolution kernel sp_kernel_precompute builds (default
  * SP_KERNEL_SUPERPOTENTIAL).  SP_KERNEL_GS_PLAIN is the original GS method without its
  * near-field correction (Sec. 1; the bracketed columns of Tab. 2): the multiplier is the
@@ -133,16 +162,47 @@ sp_status sp_solve(sp_plan plan, const void* rho, void* u, sp_stream stream);
 sp_status sp_solve_batched(sp_plan plan, const void* rho, void* u, int batch,
                            sp_stream stream);
 
-/* sp_plan_destroy -- wait for the plan's outstanding work (synchronise the plan's device)
- * and free everything it owns, from any current device (the current device is left as it
- * was).  NULL is accepted. */
+/*
+ * sp_solve_host -- `count` solves of host-resident arrays (Alg. 2 each), end to end:
+ * rho_host[i] (host, n0 x n1 x n2 of the plan's I/O type) is copied to the device, solved,
+ * and the result copied to u_host[i] (host, same shape and type), for i = 0..count-1 in
+ * order.  The copies run on two streams of the plan's own, double-buffered, so that the
+ * copy of input i+1 and of result i-1 overlap solve i on `stream`; page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) is needed for that overlap (pageable memory
+ * works, with the copies serialised by the driver).  Stream-ordered: when the work on
+ * `stream` is complete, every result is in its host array; no host synchronisation.
+ * The first call allocates the plan's four staging buffers (two inputs, two outputs),
+ * through the plan's allocator if it has one, and two copy streams; later calls reuse
+ * them.  rho_host[i] and u_host[i] may be the same array.  The host arrays must stay
+ * valid, and unread and unwritten by the host, until the work on `stream` completes.
+ */
+sp_status sp_solve_host(sp_plan plan, const void* const* rho_host, void* const* u_host, int count,
+                        sp_stream stream);
+
+/* sp_plan_destroy -- wait for the plan's own outstanding work (the last work it issued,
+ * on whichever stream; other work on the device is not waited for) and free everything it
+ * owns, from any current device (the current device is left as it was).  NULL is
+ * accepted. */
 sp_status sp_plan_destroy(sp_plan plan);
+
+/*
+ * sp_plan_sync -- host-synchronising: wait for the last work the plan issued (solves,
+ * precompute, graph launches) and report what went wrong asynchronously since the last
+ * sp_plan_sync:
+ *   SP_ERR_TIMEOUT : a kernel's bounded wait gave up (sp_solve_persistent); the status
+ *                    word is cleared, so the next sp_plan_sync returns SP_OK again;
+ *   SP_ERR_CUDA    : a device error (the CUDA context may then be unusable);
+ *   SP_OK          : otherwise.
+ * Solves return before their kernels run, so this is where errors that a kernel detects
+ * surface.
+ */
+sp_status sp_plan_sync(sp_plan plan);
 
 /* Bytes of device workspace the plan holds for solves (0 for a NULL plan). */
 size_t sp_plan_workspace_bytes(const sp_plan plan);
 
-/* Number of GS terms of the plan (known after create for an explicit table, after
- * precompute for a generated one; 0 before). */
+/* Number of GS terms of the plan (known after create: the given table's length, or the
+ * length of the table sp_kernel_precompute generates for the plan's eps). */
 int sp_plan_gs_terms(const sp_plan plan);
 
 /*
@@ -171,7 +231,10 @@ sp_status sp_forward_spectrum(sp_plan plan, const void* rho, void* spec, sp_stre
  * stream before its first pass and after each pass; sp_plan_pass_times then waits for the
  * last recorded event, adds up the elapsed time of each pass over all solves recorded
  * since the previous call, and clears the record.
- *   sp_plan_set_timing : enable != 0 turns recording on, 0 off (off by default).
+ *   sp_plan_set_timing : enable > 0 turns recording on and makes sure events for at least
+ *                        `enable` solves exist (they are created here, so that the solves
+ *                        recorded afterwards create none); 0 turns it off (the default).
+ *                        The events are kept, and reused by later records, until destroy.
  *   sp_plan_pass_times : total_ms[i] (milliseconds) and launches[i] for pass i (both
  *                        arrays of max_passes entries, either may be NULL); names[i]
  *                        (may be NULL) receives a static string naming pass i.  Returns
@@ -230,9 +293,12 @@ sp_status sp_graph_destroy(sp_graph graph);
  * of the plan's workspace.  A grid whose workspace, (16 bytes for SP_FP64 and SP_DF32,
  * else 8) x
  * n0 x 2n1 x round_up(n2 + 1, 8), exceeds it is rejected with SP_ERR_UNSUPPORTED_SIZE
- * (FP64 cubes up to n = 96 and FP32/mixed cubes up to n = 144 fit).
+ * (of the supported cube sizes, FP64 fits up to n = 126, double-float up to n = 96, its
+ * largest supported length below that, and FP32/mixed up to n = 150).
  * The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.  Every
+ * with that device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use this entry point after
+ * cudaDeviceReset (the address kept from before the reset is no longer valid).  Every
  * call shares the one array and overwrites it, so calls whose work overlaps on the
  * GPU (other streams, other threads, other plans) race and must be serialised by the
  * caller.  Stream-ordered; no host synchronisation.

@@ -31,6 +31,22 @@ _ip = ctypes.POINTER(ctypes.c_int)
 lib.sp_plan_create.restype = ctypes.c_int
 lib.sp_plan_create.argtypes = [ctypes.POINTER(_vp), _ip, _dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int,
                                ctypes.c_double, ctypes.c_int, ctypes.c_int]
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """sp_allocator of include/superpot.h."""
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+lib.sp_plan_create_ex.restype = ctypes.c_int
+lib.sp_plan_create_ex.argtypes = [ctypes.POINTER(_vp), _ip, _dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Allocator)]
+lib.sp_solve_host.restype = ctypes.c_int
+lib.sp_solve_host.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp]
+lib.sp_plan_sync.restype = ctypes.c_int
+lib.sp_plan_sync.argtypes = [_vp]
 lib.sp_kernel_precompute.restype = ctypes.c_int
 lib.sp_kernel_precompute.argtypes = [_vp, _vp]
 lib.sp_solve.restype = ctypes.c_int

@@ -40,30 +40,49 @@ static bool smooth2357(int m)
     return m == 1;
 }
 
+sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what)
+{
+    *ptr = nullptr;
+    if (p->nalloc >= (int)(sizeof(p->alloc_ptr) / sizeof(p->alloc_ptr[0])))
+        return sp_fail(SP_ERR_INVALID, "internal: too many plan allocations (%s)", what);
+    void* q = nullptr;
+    if (p->has_alloc) {
+        q = p->alloc.alloc(bytes, p->device, p->alloc.ctx);
+        if (!q) return sp_fail(SP_ERR_OOM, "allocator returned NULL for %s (%zu bytes)", what, bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // allocation failures are not sticky: clear them
+            return sp_fail(e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA, "cudaMalloc %s (%zu bytes): %s",
+                           what, bytes, cudaGetErrorName(e));
+        }
+    }
+    p->alloc_ptr[p->nalloc] = q;
+    p->alloc_bytes[p->nalloc] = bytes;
+    ++p->nalloc;
+    *ptr = q;
+    return SP_OK;
+}
+
+// Release everything the plan owns.  Its work must have completed; called with the plan's
+// device current.
 static void free_plan(sp_plan p)
 {
     if (!p) return;
-    cudaFree(p->d_gs_w);
-    cudaFree(p->d_gs_a);
-    for (int ax = 0; ax < 3; ++ax) {
-        bool owner = true;
-        for (int q = 0; q < ax; ++q)
-            if (p->d_G[q] == p->d_G[ax]) owner = false;
-        if (owner) {
-            cudaFree(p->d_G[ax]);
-            cudaFree(p->d_H[ax]);
-        }
-        cudaFree(p->d_tw64[ax]);
-        cudaFree(p->d_tw32[ax]);
-        cudaFree(p->d_twdf[ax]);
+    for (int i = p->nalloc - 1; i >= 0; --i) {
+        if (p->has_alloc) p->alloc.release(p->alloc_ptr[i], p->alloc_bytes[i], p->device, p->alloc.ctx);
+        else cudaFree(p->alloc_ptr[i]);
     }
-    cudaFree(p->d_M64);
-    cudaFree(p->d_M32);
-    cudaFree(p->d_Mdf);
-    cudaFree(p->d_work);
     if (p->ev) {
         for (cudaEvent_t e : *p->ev) cudaEventDestroy(e);
         delete p->ev;
+    }
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->staged) {
+        for (int i = 0; i < 2; ++i)
+            if (p->copy_st[i]) cudaStreamDestroy(p->copy_st[i]);
+        for (int i = 0; i < 6; ++i)
+            if (p->stage_ev[i]) cudaEventDestroy(p->stage_ev[i]);
     }
     free(p->h_gs_a);
     delete p;
@@ -77,6 +96,14 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
                                     const double* gs_a, int gs_terms, double eps,
                                     sp_precision prec, int max_batch)
 {
+    return sp_plan_create_ex(out, n, box_lo, box_hi, padding, gs_w, gs_a, gs_terms, eps, prec, max_batch, nullptr);
+}
+
+extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const double box_lo[3],
+                                       const double box_hi[3], int padding, const double* gs_w,
+                                       const double* gs_a, int gs_terms, double eps,
+                                       sp_precision prec, int max_batch, const sp_allocator* allocator)
+{
     g_err[0] = 0;
     if (!out) return sp_fail(SP_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -85,6 +112,8 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     if (prec != SP_FP64 && prec != SP_FP32 && prec != SP_MIXED && prec != SP_DF32)
         return sp_fail(SP_ERR_INVALID, "unknown precision %d", (int)prec);
     if (max_batch < 1) return sp_fail(SP_ERR_INVALID, "max_batch must be >= 1 (got %d)", max_batch);
+    if (allocator && (!allocator->alloc || !allocator->release))
+        return sp_fail(SP_ERR_INVALID, "allocator: both alloc and release must be given");
     for (int ax = 0; ax < 3; ++ax) {
         if (n[ax] < 2 || !smooth2357(2 * n[ax]) || 2 * n[ax] > kMaxLen)
             return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
@@ -111,6 +140,10 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     sp_plan p = new (std::nothrow) sp_plan_s();
     if (!p) return sp_fail(SP_ERR_OOM, "host allocation failed");
     cudaGetDevice(&p->device);
+    if (allocator) {
+        p->alloc = *allocator;
+        p->has_alloc = true;
+    }
     for (int ax = 0; ax < 3; ++ax) {
         p->n[ax] = n[ax];
         p->N[ax] = 2 * n[ax];
@@ -129,8 +162,14 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     p->h_tau = 0.1;
     p->eta = 1e-17;
     p->gs_user = user;
-    p->gs_cap = user ? gs_terms : kGsCap;
-    p->gs_terms = user ? gs_terms : 0;
+    // the generated table's length is fixed by eps and delta (eq. sin_1_x): known now
+    const int terms = user ? gs_terms : sp_gs_terms(p);
+    if (!user && (terms < 1 || terms > kGsCap)) {
+        delete p;
+        return sp_fail(SP_ERR_INVALID, "GS table of %d terms (eps %g): at most %d", terms, eps, kGsCap);
+    }
+    p->gs_cap = terms;
+    p->gs_terms = terms;
 
     p->ev = new (std::nothrow) std::vector<cudaEvent_t>();
     p->h_gs_a = (double*)malloc(sizeof(double) * p->gs_cap);
@@ -139,16 +178,37 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
         return sp_fail(SP_ERR_OOM, "host allocation failed");
     }
     if (user) memcpy(p->h_gs_a, gs_a, sizeof(double) * gs_terms);
+    else sp_gs_exponents(p, p->h_gs_a);
     sp_status rc = SP_OK;
+    if ((rc = sp_cuda_check(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming), "create plan event"))) {
+        p->done = nullptr;
+        free_plan(p);
+        return rc;
+    }
 #define SP_ALLOC(ptr, bytes)                                                           \
     do {                                                                               \
-        if ((rc = sp_cuda_check(cudaMalloc((void**)&(ptr), (bytes)), "cudaMalloc " #ptr))) { \
+        if ((rc = sp_plan_alloc(p, (void**)&(ptr), (bytes), #ptr))) {                  \
             free_plan(p);                                                              \
             return rc;                                                                 \
         }                                                                              \
     } while (0)
+    SP_ALLOC(p->d_status, 256);
     SP_ALLOC(p->d_gs_w, sizeof(double) * p->gs_cap);
     SP_ALLOC(p->d_gs_a, sizeof(double) * p->gs_cap);
+    // 1D integral tables [s][k] per axis; axes with the same (n, L) share one
+    for (int ax = 0; ax < 3; ++ax) {
+        int same = -1;
+        for (int q = 0; q < ax; ++q)
+            if (p->n[q] == p->n[ax] && p->L[q] == p->L[ax]) { same = q; break; }
+        if (same >= 0) {
+            p->d_G[ax] = p->d_G[same];
+            p->d_H[ax] = p->d_H[same];
+            continue;
+        }
+        const size_t tb = sizeof(double) * (size_t)p->gs_cap * (n[ax] + 1);
+        SP_ALLOC(p->d_G[ax], tb);
+        SP_ALLOC(p->d_H[ax], tb);
+    }
     const size_t mcount = (size_t)(n[0] + 1) * (n[1] + 1) * p->ldz;
     SP_ALLOC(p->d_M64, sizeof(double) * mcount);
     if (prec == SP_FP32 || prec == SP_MIXED) SP_ALLOC(p->d_M32, sizeof(float) * mcount);
@@ -162,6 +222,10 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     p->work_bytes = csize * (size_t)max_batch * n[0] * (size_t)p->plane;
     SP_ALLOC(p->d_work, p->work_bytes);
 #undef SP_ALLOC
+    if ((rc = sp_cuda_check(cudaMemset(p->d_status, 0, 256), "clear status word"))) {
+        free_plan(p);
+        return rc;
+    }
     if (user) {
         if ((rc = sp_cuda_check(cudaMemcpy(p->d_gs_w, gs_w, sizeof(double) * gs_terms, cudaMemcpyHostToDevice),
                                 "copy GS weights")) ||
@@ -175,6 +239,13 @@ extern "C" sp_status sp_plan_create(sp_plan* out, const int n[3], const double b
     return SP_OK;
 }
 
+sp_status sp_record_done(sp_plan p, cudaStream_t st)
+{
+    sp_status rc = sp_cuda_check(cudaEventRecord(p->done, st), "record plan event");
+    if (rc == SP_OK) p->done_recorded = true;
+    return rc;
+}
+
 extern "C" sp_status sp_kernel_precompute(sp_plan p, sp_stream stream)
 {
     g_err[0] = 0;
@@ -186,6 +257,7 @@ extern "C" sp_status sp_kernel_precompute(sp_plan p, sp_stream stream)
     if ((rc = sp_cuda_check(cudaMemsetAsync(p->d_M64, 0, sizeof(double) * mcount, st), "clear multiplier")))
         return rc;
     if ((rc = sp_setup_run(p, st))) return rc;
+    if ((rc = sp_record_done(p, st))) return rc;
     p->ready = true;
     return SP_OK;
 }
@@ -226,7 +298,8 @@ extern "C" sp_status sp_solve(sp_plan p, const void* rho, void* u, sp_stream str
     g_err[0] = 0;
     sp_status rc = check_solve_args(p, rho, u);
     if (rc) return rc;
-    return sp_run_solve(p, rho, u, 1, (cudaStream_t)stream);
+    if ((rc = sp_run_solve(p, rho, u, 1, (cudaStream_t)stream))) return rc;
+    return sp_record_done(p, (cudaStream_t)stream);
 }
 
 extern "C" sp_status sp_solve_batched(sp_plan p, const void* rho, void* u, int batch, sp_stream stream)
@@ -236,7 +309,8 @@ extern "C" sp_status sp_solve_batched(sp_plan p, const void* rho, void* u, int b
     if (rc) return rc;
     if (batch < 1 || batch > p->max_batch)
         return sp_fail(SP_ERR_INVALID, "batch %d outside [1, max_batch = %d]", batch, p->max_batch);
-    return sp_run_solve(p, rho, u, batch, (cudaStream_t)stream);
+    if ((rc = sp_run_solve(p, rho, u, batch, (cudaStream_t)stream))) return rc;
+    return sp_record_done(p, (cudaStream_t)stream);
 }
 
 extern "C" sp_status sp_forward_spectrum(sp_plan p, const void* rho, void* spec, sp_stream stream)
@@ -244,21 +318,43 @@ extern "C" sp_status sp_forward_spectrum(sp_plan p, const void* rho, void* spec,
     g_err[0] = 0;
     sp_status rc = check_solve_args(p, rho, spec);
     if (rc) return rc;
-    return sp_run_forward(p, rho, spec, (cudaStream_t)stream);
+    if ((rc = sp_run_forward(p, rho, spec, (cudaStream_t)stream))) return rc;
+    return sp_record_done(p, (cudaStream_t)stream);
 }
 
 extern "C" sp_status sp_plan_destroy(sp_plan p)
 {
     g_err[0] = 0;
     if (!p) return SP_OK;
-    // wait for and free on the plan's own device, whichever device is current
+    // wait for the plan's own last work and free on the plan's device, whichever device is
+    // current
     int cur = -1;
     const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
                           cudaSetDevice(p->device) == cudaSuccess;
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = p->done_recorded ? cudaEventSynchronize(p->done) : cudaSuccess;
     free_plan(p);
     if (switched) cudaSetDevice(cur);
-    return sp_cuda_check(e, "synchronise before destroy");
+    return sp_cuda_check(e, "wait for the plan's work before destroy");
+}
+
+extern "C" sp_status sp_plan_sync(sp_plan p)
+{
+    g_err[0] = 0;
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    sp_status rc = sp_check_device(p);
+    if (rc) return rc;
+    if (p->done_recorded && (rc = sp_cuda_check(cudaEventSynchronize(p->done), "wait for the plan's work")))
+        return rc;
+    if ((rc = sp_cuda_check(cudaGetLastError(), "pending device error"))) return rc;
+    int status = 0;
+    if ((rc = sp_cuda_check(cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status word")))
+        return rc;
+    if (status != 0) {
+        if ((rc = sp_cuda_check(cudaMemset(p->d_status, 0, sizeof(int)), "clear status word"))) return rc;
+        return sp_fail(SP_ERR_TIMEOUT, "a bounded device wait gave up (status %d): some work of the solve was not done",
+                       status);
+    }
+    return SP_OK;
 }
 
 extern "C" size_t sp_plan_workspace_bytes(const sp_plan p) { return p ? p->work_bytes : 0; }
@@ -273,7 +369,9 @@ extern "C" sp_status sp_plan_copy_tables(sp_plan p, double* gs_w, double* gs_a, 
     if (!p->ready) return sp_fail(SP_ERR_NOT_READY, "sp_kernel_precompute has not been run on this plan");
     if ((G || H) && (axis < 0 || axis > 2)) return sp_fail(SP_ERR_INVALID, "axis must be 0, 1 or 2");
     sp_status rc;
-    if ((rc = sp_cuda_check(cudaDeviceSynchronize(), "synchronise before copy"))) return rc;
+    if ((rc = sp_check_device(p))) return rc;
+    if (p->done_recorded && (rc = sp_cuda_check(cudaEventSynchronize(p->done), "wait for the plan's work")))
+        return rc;
     const int S = p->gs_terms;
     if (gs_w && (rc = sp_cuda_check(cudaMemcpy(gs_w, p->d_gs_w, sizeof(double) * S, cudaMemcpyDeviceToHost),
                                     "copy GS weights")))
@@ -301,18 +399,39 @@ extern "C" sp_status sp_plan_copy_tables(sp_plan p, double* gs_w, double* gs_a, 
 sp_status sp_mark(sp_plan p, cudaStream_t st)
 {
     if (!p->timing) return SP_OK;
-    cudaEvent_t e;
-    sp_status rc = sp_cuda_check(cudaEventCreate(&e), "create timing event");
-    if (rc) return rc;
-    p->ev->push_back(e);
-    return sp_cuda_check(cudaEventRecord(e, st), "record timing event");
+    std::vector<cudaEvent_t>& ev = *p->ev;
+    if (p->ev_used == ev.size()) {  // the pool is exhausted: grow it (outside a reserved record)
+        cudaEvent_t e;
+        sp_status rc = sp_cuda_check(cudaEventCreate(&e), "create timing event");
+        if (rc) return rc;
+        ev.push_back(e);
+    }
+    return sp_cuda_check(cudaEventRecord(ev[p->ev_used++], st), "record timing event");
+}
+
+// Events for `solves` recorded solves (npass + 1 each; 8 passes assumed before the first
+// solve tells the pass count).
+static sp_status reserve_events(sp_plan p, int solves)
+{
+    const int per = (p->npass > 0 ? p->npass : 8) + 1;
+    const size_t want = p->ev_used + (size_t)solves * per;
+    std::vector<cudaEvent_t>& ev = *p->ev;
+    while (ev.size() < want) {
+        cudaEvent_t e;
+        sp_status rc = sp_cuda_check(cudaEventCreate(&e), "create timing event");
+        if (rc) return rc;
+        ev.push_back(e);
+    }
+    return SP_OK;
 }
 
 extern "C" sp_status sp_plan_set_timing(sp_plan p, int enable)
 {
     g_err[0] = 0;
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (enable < 0) return sp_fail(SP_ERR_INVALID, "enable must be >= 0 (got %d)", enable);
     p->timing = enable != 0;
+    if (enable > 0) return reserve_events(p, enable);
     return SP_OK;
 }
 
@@ -329,10 +448,11 @@ extern "C" int sp_plan_pass_times(sp_plan p, double* total_ms, int* launches, co
         if (names) names[i] = p->pass_name[i];
     }
     std::vector<cudaEvent_t>& ev = *p->ev;
-    if (np == 0 || ev.empty()) return np;
-    if (ev.size() % per != 0) { sp_fail(SP_ERR_INVALID, "incomplete timing record"); return -1; }
-    if (sp_cuda_check(cudaEventSynchronize(ev.back()), "wait for timing events")) return -1;
-    for (size_t s0 = 0; s0 < ev.size(); s0 += per) {
+    const size_t used = p->ev_used;
+    if (np == 0 || used == 0) return np;
+    if (used % per != 0) { sp_fail(SP_ERR_INVALID, "incomplete timing record"); return -1; }
+    if (sp_cuda_check(cudaEventSynchronize(ev[used - 1]), "wait for timing events")) return -1;
+    for (size_t s0 = 0; s0 < used; s0 += per) {
         for (int i = 0; i < np; ++i) {
             float ms = 0.f;
             if (sp_cuda_check(cudaEventElapsedTime(&ms, ev[s0 + i], ev[s0 + i + 1]), "elapsed time"))
@@ -343,8 +463,7 @@ extern "C" int sp_plan_pass_times(sp_plan p, double* total_ms, int* launches, co
             }
         }
     }
-    for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    ev.clear();
+    p->ev_used = 0;  // the events stay in the pool for the next record
     return np;
 }
 

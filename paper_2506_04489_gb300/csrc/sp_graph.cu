@@ -14,6 +14,7 @@
 struct sp_graph_s {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    sp_plan plan;  // its completion event is recorded after every replay
 };
 
 static float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
@@ -110,15 +111,18 @@ extern "C" sp_status sp_graph_capture(sp_plan p, const void* rho, void* u, int b
     }
     g->graph = graph;
     g->exec = exec;
+    g->plan = p;
     *out = g;
-    return SP_OK;
+    return sp_record_done(p, st);
 }
 
 extern "C" sp_status sp_graph_launch(sp_graph g, sp_stream stream)
 {
     sp_clear_error();
     if (!g) return sp_fail(SP_ERR_INVALID, "graph is NULL");
-    return sp_cuda_check(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+    sp_status rc = sp_cuda_check(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+    if (rc) return rc;
+    return sp_record_done(g->plan, (cudaStream_t)stream);
 }
 
 extern "C" sp_status sp_graph_destroy(sp_graph g)

@@ -48,21 +48,48 @@ struct sp_plan_s {
     bool ready;
     int device;
     int kernel;      // sp_kernel
+    // the plan's last recorded work: every entry point that issues work on a stream records
+    // this event after it, so destroy and sp_plan_sync wait for the plan alone
+    cudaEvent_t done;
+    bool done_recorded;
+    // device status word: set by a kernel whose bounded wait gave up (SP_ERR_TIMEOUT),
+    // read and cleared by sp_plan_sync
+    int* d_status;
+    // device memory of the plan: every allocation, released in reverse order at destroy,
+    // through the caller's allocator when one was given, else cudaFree
+    sp_allocator alloc;
+    bool has_alloc;
+    int nalloc;
+    void* alloc_ptr[32];
+    size_t alloc_bytes[32];
+    // sp_solve_host staging (created by its first call): two input and two output device
+    // buffers, a host-to-device and a device-to-host copy stream, and their events
+    void* d_stage[4];
+    cudaStream_t copy_st[2];
+    cudaEvent_t stage_ev[6];  // loaded[2], solved[2], fetched[2]
+    bool staged;
     // tiles of the register-resident passes (0 = built-in default): columns per CTA of
     // the line passes per axis, pairs of real lines per CTA of the z passes
     int tile_line[3];
     int tile_z;
-    // pass timing (diagnostic): events recorded between passes while timing is on
+    // pass timing (diagnostic): events recorded between passes while timing is on.  The
+    // events are a pool kept for the plan's life: ev_used of them hold the current record
+    // ((npass + 1) per recorded solve); the pool grows only when a record outruns it.
     bool timing;
     int npass;                          // passes of one solve
     const char* pass_name[8];
-    std::vector<cudaEvent_t>* ev;       // (npass + 1) events per recorded solve
+    std::vector<cudaEvent_t>* ev;
+    size_t ev_used;
     // Every member is a plain value or pointer, so a copy of the struct is a plain
     // byte copy that allocates nothing.
 };
 
 // Record a timing event on `st` if the plan is timing (no-op otherwise).
 sp_status sp_mark(sp_plan p, cudaStream_t st);
+// Record the plan's completion event on `st` after work issued there.
+sp_status sp_record_done(sp_plan p, cudaStream_t st);
+// Device allocation owned by the plan (the caller's allocator, else cudaMalloc).
+sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what);
 
 // Thread-local error message helpers (sp_api.cu).
 void sp_clear_error(void);
@@ -72,6 +99,10 @@ sp_status sp_check_device(const sp_plan p);  // SP_ERR_INVALID unless p's device
 
 // Setup (sp_setup.cu).  All FP64.
 sp_status sp_setup_run(sp_plan p, cudaStream_t st);
+// Length of the generated GS table for the plan's eps and delta, and its exponents a_s
+// (host, the same values the GPU generates up to rounding of exp).
+int sp_gs_terms(const sp_plan p);
+void sp_gs_exponents(const sp_plan p, double* a);
 
 // Register-resident solve passes for the compiled lengths (sp_v2_*.cu); they return
 // SP_ERR_UNSUPPORTED_SIZE, with no message, when an axis length has no compiled plan.

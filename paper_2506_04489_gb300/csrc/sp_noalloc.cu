@@ -12,8 +12,10 @@
 //
 // The scratch is one array per GPU that loads the library, held until the process
 // exits.  Its device address is looked up once per device (cudaGetSymbolAddress,
-// with that device current) on the first call made while it is the current device;
-// make that first call before any stream capture.  All calls share the array, so
+// with that device current) on the first call made while it is the current device,
+// and kept for the life of the process: make that first call before any stream
+// capture, and do not call this entry point after cudaDeviceReset, which invalidates
+// the kept address.  All calls share the array, so
 // calls whose work overlaps on the GPU (other streams, other host threads, other
 // plans) race on it and must be serialised by the caller.  No part of the scratch has
 // to start at zero: every element a pass reads was written earlier in the same call.
@@ -76,5 +78,8 @@ extern "C" sp_status sp_solve_noalloc(const sp_plan p, const void* rho, void* u,
     view.work_bytes = need;
     view.max_batch = 1;
     view.timing = false;
-    return sp_run_solve(&view, rho, u, 1, (cudaStream_t)stream);
+    if ((rc = sp_run_solve(&view, rho, u, 1, (cudaStream_t)stream))) return rc;
+    // the plan's completion event (recording it allocates nothing): sp_plan_destroy
+    // waits for it before freeing the multiplier and twiddles this solve reads
+    return sp_record_done(p, (cudaStream_t)stream);
 }

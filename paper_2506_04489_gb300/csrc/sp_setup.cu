@@ -373,41 +373,52 @@ static sp_status setup_axis(sp_plan p, int ax, cudaStream_t st)
     return sp_cuda_check(cudaGetLastError(), "setup: full-line kernel");
 }
 
+// GS table of eq. (sin_1_x) for the plan's (eps, delta): tau_s = tau_lo + s h_tau for
+// s = 0..terms-1 (reading of the paper's sinc quadrature, see k_gs_table).
+static void gs_range(const sp_plan p, double* tau_lo, int* terms)
+{
+    *tau_lo = log(p->eta * sqrt(kPi) / (2.0 * p->delta));
+    const double tau_hi = log(sqrt(log(1.0 / p->eta)) / p->eps) + 0.5;
+    *terms = (int)ceil((tau_hi - *tau_lo) / p->h_tau) + 1;
+}
+
+int sp_gs_terms(const sp_plan p)
+{
+    double tau_lo;
+    int terms;
+    gs_range(p, &tau_lo, &terms);
+    return terms;
+}
+
+void sp_gs_exponents(const sp_plan p, double* a)
+{
+    double tau_lo;
+    int terms;
+    gs_range(p, &tau_lo, &terms);
+    for (int s = 0; s < terms; ++s) a[s] = exp(2.0 * (tau_lo + s * p->h_tau));
+}
+
 sp_status sp_setup_run(sp_plan p, cudaStream_t st)
 {
     sp_status rc;
     // K4: GS table (unless the caller supplied one at plan creation)
     if (!p->gs_user) {
-        double tau_lo = log(p->eta * sqrt(kPi) / (2.0 * p->delta));
-        double tau_hi = log(sqrt(log(1.0 / p->eta)) / p->eps) + 0.5;
-        int terms = (int)ceil((tau_hi - tau_lo) / p->h_tau) + 1;
-        if (terms > p->gs_cap) return sp_fail(SP_ERR_INVALID, "GS table longer than %d terms", p->gs_cap);
+        double tau_lo;
+        int terms;
+        gs_range(p, &tau_lo, &terms);
+        if (terms != p->gs_terms) return sp_fail(SP_ERR_INVALID, "internal: GS table length changed");
         k_gs_table<<<nblk(terms, 128), 128, 0, st>>>(tau_lo, p->h_tau, terms, p->d_gs_w, p->d_gs_a);
-        p->gs_terms = terms;
-        for (int s = 0; s < terms; ++s) p->h_gs_a[s] = exp(2.0 * (tau_lo + s * p->h_tau));
         if ((rc = sp_cuda_check(cudaGetLastError(), "GS table kernel"))) return rc;
     }
-    const int S = p->gs_terms;
-    // per-axis tables (allocated here: their size depends on S)
+    // per-axis tables (allocated with the plan; axes with the same (n, L) share one)
     for (int ax = 0; ax < 3; ++ax) {
-        int same = -1;
+        bool shared = false;
         for (int q = 0; q < ax; ++q)
-            if (p->n[q] == p->n[ax] && p->L[q] == p->L[ax]) { same = q; break; }
-        if (p->d_G[ax] && (same < 0 || p->d_G[ax] != p->d_G[same])) {
-            cudaFree(p->d_G[ax]);
-            cudaFree(p->d_H[ax]);
-        }
-        p->d_G[ax] = p->d_H[ax] = nullptr;
-        if (same >= 0) {
-            p->d_G[ax] = p->d_G[same];
-            p->d_H[ax] = p->d_H[same];
-            continue;
-        }
-        size_t bytes = sizeof(double) * (size_t)S * (p->n[ax] + 1);
-        if (cudaMalloc(&p->d_G[ax], bytes) != cudaSuccess || cudaMalloc(&p->d_H[ax], bytes) != cudaSuccess)
-            return sp_fail(SP_ERR_OOM, "setup: 1D table allocation failed");
+            if (p->d_G[q] == p->d_G[ax]) shared = true;
+        if (shared) continue;
         if ((rc = setup_axis(p, ax, st))) return rc;
     }
+    const int S = p->gs_terms;
     // K6: multiplier, GEMM over the 2S GS columns, in row chunks
     {
         const int n0p = p->n[0] + 1, n1p = p->n[1] + 1, n2p = p->n[2] + 1;

@@ -718,7 +718,9 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
 
 // Time `iters` launches of one pass (0: z passes, 1: y passes, 2: x pass) with the
 // given tile, on the plan's workspace (contents irrelevant: the arithmetic does not
-// depend on the data), `batch` right-hand sides.  Host-synchronising.  Returns the mean
+// depend on the data), `batch` right-hand sides (the z passes of every right-hand side
+// read and write one dummy input and output inside the workspace, the line passes their
+// own workspace slices, as in the solve).  Host-synchronising.  Returns the mean
 // milliseconds per launch, or a negative value on error.
 template <class R, class Tio>
 float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
@@ -759,9 +761,9 @@ float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_
     sp_status rc = SP_OK;
     for (int it = -1; it < iters && rc == SP_OK; ++it) {  // it = -1: warm-up launch
         if (it == 0) cudaEventRecord(e0, st);
-        if (pass == 0) {
-            rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, 1, st});
-            if (rc == SP_OK) rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, 1, st});
+        if (pass == 0) {  // every right-hand side reads the same input and writes the same output
+            rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, batch, st});
+            if (rc == SP_OK) rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, batch, st});
         } else if (pass == 1) {
             rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st});
             if (rc == SP_OK) rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st});

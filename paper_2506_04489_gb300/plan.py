@@ -22,6 +22,31 @@ def _vec3(v):
     return v
 
 
+def torch_empty_pinned(shape, dtype):
+    import torch
+    return torch.empty(shape, dtype=dtype, pin_memory=True)
+
+
+def torch_allocator():
+    """An sp_allocator drawing on PyTorch's CUDA caching allocator (argument marshalling
+    only: the callbacks hand torch's blocks to the library and give them back)."""
+    from . import _native as N
+
+    def alloc(nbytes, device, ctx):
+        import torch
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device)))
+        except Exception:
+            return None
+
+    def release(ptr, nbytes, device, ctx):
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cb = N.Allocator(N.ALLOC_FN(alloc), N.RELEASE_FN(release), None)
+    return cb
+
+
 def _stream_handle(stream):
     import torch
     if stream is None:
@@ -41,10 +66,13 @@ class Plan:
     precompute: run Alg. 1 on the current stream at construction.
     kernel    : "superpotential" (the paper's method) or "gs_plain" (the original GS
                 method without near-field correction, for comparison).
+    allocator : None (the library allocates with cudaMalloc) or "torch" (the plan's device
+                memory comes from PyTorch's caching allocator, sp_plan_create_ex).
     """
 
     def __init__(self, n, lo, hi, precision: str = "fp64", eps: float = 1e-4, gs=None,
-                 max_batch: int = 1, precompute: bool = True, stream=None, kernel: str = "superpotential"):
+                 max_batch: int = 1, precompute: bool = True, stream=None, kernel: str = "superpotential",
+                 allocator=None):
         from . import _native as N
         self._N = N
         if precision not in _PREC:
@@ -65,8 +93,14 @@ class Plan:
             wp = ap = None
             terms = 0
         h = ctypes.c_void_p()
-        N.check(N.lib.sp_plan_create(ctypes.byref(h), n_c, lo_c, hi_c, 2, wp, ap, terms, float(eps),
-                                     _PREC[precision], self.max_batch), "sp_plan_create")
+        if allocator not in (None, "torch"):
+            raise ValueError("allocator must be None or 'torch'")
+        # the callbacks must outlive the plan: keep them on it
+        self._allocator = torch_allocator() if allocator == "torch" else None
+        N.check(N.lib.sp_plan_create_ex(ctypes.byref(h), n_c, lo_c, hi_c, 2, wp, ap, terms, float(eps),
+                                        _PREC[precision], self.max_batch,
+                                        ctypes.byref(self._allocator) if self._allocator else None),
+                "sp_plan_create_ex")
         self._h = h
         self.dtype = precision_dtype(precision)
         if kernel not in ("superpotential", "gs_plain"):
@@ -80,6 +114,11 @@ class Plan:
     # ----------------------------------------------------------------- lifecycle
     def precompute(self, stream=None) -> None:
         self._N.check(self._N.lib.sp_kernel_precompute(self._h, _stream_handle(stream)), "sp_kernel_precompute")
+
+    def sync(self) -> None:
+        """Wait for the plan's last work and raise on an error its kernels reported
+        (sp_plan_sync: SP_ERR_TIMEOUT for a bounded wait that gave up)."""
+        self._N.check(self._N.lib.sp_plan_sync(self._h), "sp_plan_sync")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -136,19 +175,9 @@ class Plan:
         return out
 
     def _solve_host(self, rho, out, stream):
-        import torch
-        if rho.dtype != self.dtype or tuple(rho.shape) != self.n or not rho.is_contiguous():
-            raise ValueError(f"expected a contiguous {self.dtype} tensor of shape {self.n}")
-        st = stream if stream is not None else torch.cuda.current_stream()
-        buf = getattr(self, "_stage", None)
-        if buf is None:
-            buf = self._stage = torch.empty(self.n, dtype=self.dtype, device="cuda")
         if out is None:
-            out = torch.empty(self.n, dtype=self.dtype, pin_memory=True)
-        with torch.cuda.stream(st):
-            buf.copy_(rho, non_blocking=True)
-            self.solve(buf, buf, st)
-            out.copy_(buf, non_blocking=True)
+            out = torch_empty_pinned(self.n, self.dtype)
+        self.solve_host_stream([rho], [out], stream, wait=False)
         return out
 
     # ----------------------------------------------------------------- batched execution
@@ -174,13 +203,12 @@ class Plan:
                       "sp_graph_capture")
         return Graph(self, g, (rho, out))
 
-    def solve_host_stream(self, inputs, outputs, stream=None):
-        """Solve a sequence of CPU densities into CPU outputs (pinned tensors of the plan's
-        shape and dtype), overlapping the host-to-device copy of input i+1 and the
-        device-to-host copy of result i-1 with the solve of i.  The solves run in order
-        on ``stream`` (the plan has one workspace); each copy direction has a stream of
-        its own, two device buffers per direction.  Returns after the last result is on
-        the host."""
+    def solve_host_stream(self, inputs, outputs, stream=None, wait: bool = True):
+        """Solve a sequence of CPU densities into CPU outputs (contiguous tensors of the
+        plan's shape and dtype, pinned for overlap) through sp_solve_host: the copy of
+        input i+1 and of result i-1 overlap the solve of i.  With ``wait`` (default) it
+        returns after the last result is on the host; else the results are complete when
+        the work on ``stream`` is."""
         import torch
         if len(inputs) != len(outputs):
             raise ValueError("inputs and outputs must have the same length")
@@ -188,43 +216,21 @@ class Plan:
             if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != self.n \
                     or not t.is_contiguous():
                 raise ValueError(f"expected contiguous CPU {self.dtype} tensors of shape {self.n}")
-        solve_st = stream if stream is not None else torch.cuda.current_stream()
-        if getattr(self, "_copy_streams", None) is None:
-            self._copy_streams = (torch.cuda.Stream(), torch.cuda.Stream())
-            self._stream_bufs = [torch.empty(self.n, dtype=self.dtype, device="cuda") for _ in range(4)]
-        h2d, d2h = self._copy_streams
-        dev_in, dev_out = self._stream_bufs[:2], self._stream_bufs[2:]
-        h2d.wait_stream(torch.cuda.current_stream())  # buffers made on the current stream
-        d2h.wait_stream(torch.cuda.current_stream())
         n = len(inputs)
-        loaded = [torch.cuda.Event() for _ in range(2)]
-        solved = [torch.cuda.Event() for _ in range(2)]
-        fetched = [torch.cuda.Event() for _ in range(2)]
-        for i in range(n + 1):
-            if i < n:  # input i, once solve i-2 has released its buffer
-                k = i % 2
-                if i >= 2:
-                    h2d.wait_event(solved[k])
-                with torch.cuda.stream(h2d):
-                    dev_in[k].copy_(inputs[i], non_blocking=True)
-                    loaded[k].record(h2d)
-            if i >= 1:  # solve i-1 once its input is in and result i-3 is out
-                j = (i - 1) % 2
-                solve_st.wait_event(loaded[j])
-                if i - 1 >= 2:
-                    solve_st.wait_event(fetched[j])
-                self.solve(dev_in[j], dev_out[j], solve_st)
-                solved[j].record(solve_st)
-                d2h.wait_event(solved[j])
-                with torch.cuda.stream(d2h):
-                    outputs[i - 1].copy_(dev_out[j], non_blocking=True)
-                    fetched[j].record(d2h)
-        d2h.synchronize()
+        rin = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in inputs])
+        rout = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in outputs])
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._N.check(self._N.lib.sp_solve_host(self._h, rin, rout, n, ctypes.c_void_p(st.cuda_stream)),
+                      "sp_solve_host")
+        if wait:
+            st.synchronize()
         return outputs
 
     # ----------------------------------------------------------------- diagnostics
-    def set_timing(self, enable: bool) -> None:
-        self._N.check(self._N.lib.sp_plan_set_timing(self._h, int(bool(enable))), "sp_plan_set_timing")
+    def set_timing(self, enable, reserve: int = 1) -> None:
+        """Turn pass timing on (events for `reserve` solves created now) or off."""
+        n = max(1, int(reserve)) if enable else 0
+        self._N.check(self._N.lib.sp_plan_set_timing(self._h, n), "sp_plan_set_timing")
 
     def pass_times(self):
         """{pass name: (total ms, launches)} over the solves recorded since the last call."""

@@ -63,3 +63,17 @@ def test_rejects_invalid_arguments(native):
     assert native.lib.sp_solve(None, None, None, None) == 1
     assert native.lib.sp_plan_destroy(None) == 0
     assert native.lib.sp_plan_workspace_bytes(None) == 0
+
+
+def test_new_entry_points_reject_invalid_arguments(native):
+    # allocator without callbacks: refused before any device memory is touched
+    h = ctypes.c_void_p()
+    nn = (ctypes.c_int * 3)(8, 8, 8)
+    lo = (ctypes.c_double * 3)(-1, -1, -1)
+    hi = (ctypes.c_double * 3)(1, 1, 1)
+    bad = native.Allocator()
+    assert native.lib.sp_plan_create_ex(ctypes.byref(h), nn, lo, hi, 2, None, None, 0, 1e-4, 0, 1,
+                                        ctypes.byref(bad)) == 1
+    assert not h.value and b"allocator" in native.lib.sp_last_error()
+    assert native.lib.sp_plan_sync(None) == 1
+    assert native.lib.sp_solve_host(None, None, None, 1, None) == 1

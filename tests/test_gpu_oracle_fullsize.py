@@ -1,0 +1,126 @@
+"""Element-by-element parity with the FP64 oracle at the benchmark sizes.
+
+The oracle (Alg. 2 on the full zero-padded (2n)^3 grid, its own FFT) runs whole here:
+at 256^3 (the headline workload), 192^3 (padded 384, the served size with a factor 3)
+and 512^3 (the single large solve; it needs about 20 GB of host memory and is skipped,
+with the reason, when the host has less than twice that free).  Each CUDA result is
+compared at every grid point, max-norm relative: FP64 and double-float to 1e-12, FP32 and
+mixed precision to 1e-5.  The 256^3 cases run with the built-in tiles and with the tiles
+the benchmark's autotuner picks, so both the pipelined and the plain line kernels meet
+the oracle at the timed size.  Densities: the C-infinity bump plus seeded noise on its
+support (symmetry broken), and a seeded Gaussian mixture plus white noise on the whole box
+(every wavenumber present).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2506_04489_gb300 import Plan, workloads as W  # noqa: E402
+
+TOL = {"fp64": 1e-12, "df32": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+LO, HI = -1.0, 1.0
+
+
+def _bump_noisy(n):
+    rho = W.bump_profile(n, LO, HI)
+    rng = np.random.default_rng(n)
+    return rho + 1e-3 * rng.standard_normal(rho.shape) * (rho > 0)
+
+
+def _mixture_noise(n):
+    rng = np.random.default_rng(n + 1)
+    return W.gaussian_mixture(n, LO, HI, 3) + 1e-2 * rng.standard_normal((n, n, n))
+
+
+DENSITIES = {"bump_noisy": _bump_noisy, "mixture_noise": _mixture_noise}
+_tables = {}  # multiplier of one grid size
+_cases = {}   # (density, oracle potential) of one (size, density)
+
+
+def _oracle_case(oracle, n, dens):
+    if n not in _tables:
+        _tables.clear()
+        _cases.clear()
+        _tables[n] = oracle.plan_tables(n, LO, HI)[2]
+    key = (n, dens)
+    if key not in _cases:
+        _cases.clear()  # one full-size case held at a time
+        rho = DENSITIES[dens](n)
+        _cases[key] = (rho, oracle.solve(_tables[n], rho))
+    return _cases[key]
+
+
+def _rel(u, ref):
+    return float(np.abs(u - ref).max() / np.abs(ref).max())
+
+
+def _solve(plan, rho):
+    u = plan.solve(torch.from_numpy(rho).to("cuda", dtype=plan.dtype))
+    plan.sync()
+    return u.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dens", sorted(DENSITIES))
+@pytest.mark.parametrize("precision", ["df32", "fp64", "fp32", "mixed"])
+def test_256_against_oracle(oracle, dens, precision, record_property):
+    n = 256
+    rho, ref = _oracle_case(oracle, n, dens)
+    plan = Plan(n, LO, HI, precision=precision)
+    e_default = _rel(_solve(plan, rho), ref)
+    tiles = plan.autotune(1)  # the benchmark's launch configuration
+    e_tuned = _rel(_solve(plan, rho), ref)
+    plan.close()
+    record_property("max_rel_err", (e_default, e_tuned))
+    print(f"256^3 {dens} {precision}: max-norm rel err vs oracle {e_default:.3e} (built-in tiles), "
+          f"{e_tuned:.3e} (autotuned {tiles})")
+    assert e_default <= TOL[precision]
+    assert e_tuned <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["df32", "fp64", "fp32", "mixed"])
+def test_192_against_oracle(oracle, precision):
+    n = 192
+    rho, ref = _oracle_case(oracle, n, "mixture_noise")
+    plan = Plan(n, LO, HI, precision=precision)
+    e = _rel(_solve(plan, rho), ref)
+    plan.autotune(1)
+    e2 = _rel(_solve(plan, rho), ref)
+    plan.close()
+    print(f"192^3 mixture_noise {precision}: max-norm rel err vs oracle {e:.3e} / {e2:.3e} (autotuned)")
+    assert e <= TOL[precision] and e2 <= TOL[precision]
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def test_512_against_oracle(oracle):
+    # 512^3 bump (the single large solve): the double-float path at the FP64 bar and the
+    # mixed-precision path (FP32 passes, FP64 in/out) at the FP32 bar, each against the
+    # oracle's full solve; the mixed path's error is the figure the configuration asks
+    # to state.
+    n = 512
+    need = 2 * (16 * (2 * n) ** 3 + 8 * (n + 1) ** 3 + 4 * 8 * n ** 3)
+    have = _mem_available_bytes()
+    if have < need:
+        pytest.skip(f"host has {have / 1e9:.0f} GB available; the 512^3 oracle wants {need / 2e9:.0f} GB (x2)")
+    rho, ref = _oracle_case(oracle, n, "bump_noisy")
+    errs = {}
+    for precision in ("df32", "mixed"):
+        plan = Plan(n, LO, HI, precision=precision)
+        plan.autotune(1)
+        errs[precision] = _rel(_solve(plan, rho), ref)
+        plan.close()
+        torch.cuda.empty_cache()
+    print(f"512^3 bump_noisy: max-norm rel err vs oracle: df32 {errs['df32']:.3e}, mixed {errs['mixed']:.3e}")
+    assert errs["df32"] <= TOL["df32"]
+    assert errs["mixed"] <= TOL["mixed"]

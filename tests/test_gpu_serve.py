@@ -82,3 +82,29 @@ def test_results_into_caller_buffers():
         assert g.data_ptr() == o.data_ptr()
         assert torch.equal(o, plan.solve(r.cuda()).cpu())
     plan.close()
+
+
+def test_large_sizes_in_the_mix_equal_alone():
+    # the served sizes where the latency tail lives (128^3, 192^3, 256^3) mixed with small
+    # ones, both accuracies: each result equals the same solve alone, bit for bit
+    srv = serve.Server(budget_bytes=40e9, max_batch=4, slots=4).start()
+    rng = np.random.default_rng(1)
+    sizes = (32, 128, 192, 256)
+    reqs = []
+    for i in range(24):
+        n = int(sizes[rng.integers(len(sizes))])
+        acc = (1e-6, 1e-12)[int(rng.integers(2))]
+        rho = _density(n, 100 + i, serve.precision_for(acc))
+        reqs.append((n, acc, rho, srv.submit(rho, acc)))
+        if i % 6 == 5:
+            time.sleep(0.005)
+    results = [f.result(timeout=300) for *_, f in reqs]
+    srv.stop()
+    plans = {}
+    for (n, acc, rho, _), u in zip(reqs, results):
+        key = (n, serve.precision_for(acc))
+        if key not in plans:
+            plans[key] = Plan(n, -1.0, 1.0, precision=key[1])
+        assert torch.equal(u, plans[key].solve(rho.cuda()).cpu()), key
+    for p in plans.values():
+        p.close()

@@ -51,7 +51,7 @@ def test_max_over_ranks_and_barrier_gloo():
 def test_reference_arm_under_torchrun_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--grid", "32"]
     env = dict(os.environ, OMP_NUM_THREADS=str(max(1, (os.cpu_count() or 2) // 2)))
     p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert p.returncode == 0, p.stderr[-2000:]
@@ -59,4 +59,11 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
-    assert rec["cpu_baseline"]["kind"] == "oracle"
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
+    # the same metric, unit and direction as the GPU arm, so that the two lines compare
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_ref_check", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert rec["metric"] == bench.METRIC and rec["unit"] == "grid pts/s" and rec["higher_is_better"] is True
+    assert rec["config"] == bench.workload_config(32, 2)
