@@ -82,7 +82,9 @@ typedef void* sp_stream; /* a cudaStream_t */
  *                is sized for it.
  * Device memory: multiplier octant (n0+1)(n1+1)(n2+1) FP64 (+ an FP32 or double-float
  * copy for those passes), twiddles, and a workspace of n0 * 2n1 * (n2+1) complex values
- * per batch element (see sp_plan_workspace_bytes).  Allocated on the current device.
+ * per batch element (see sp_plan_workspace_bytes).  Allocated on the current device,
+ * stream-ordered from its default memory pool (cudaMallocAsync on a stream of the plan's
+ * own, complete when this call returns); sp_plan_create_ex takes a caller's allocator.
  * SP_DF32 plans need every 2n in {64, 128, 192, 256, 384, 512, 1024}
  * (else SP_ERR_UNSUPPORTED_SIZE).
  */
@@ -179,10 +181,12 @@ sp_status sp_solve_batched(sp_plan plan, const void* rho, void* u, int batch,
 sp_status sp_solve_host(sp_plan plan, const void* const* rho_host, void* const* u_host, int count,
                         sp_stream stream);
 
-/* sp_plan_destroy -- wait for the plan's own outstanding work (the last work it issued,
- * on whichever stream; other work on the device is not waited for) and free everything it
- * owns, from any current device (the current device is left as it was).  NULL is
- * accepted. */
+/* sp_plan_destroy -- release everything the plan owns once its own outstanding work (the
+ * last work it issued, on whichever stream) has completed, from any current device (the
+ * current device is left as it was).  Other work on the device is never waited for: the
+ * library's own device memory is freed stream-ordered after that work (cudaFreeAsync,
+ * no host wait); with a caller's allocator, destroy waits on the host for the plan's
+ * work alone and then hands the blocks back.  NULL is accepted. */
 sp_status sp_plan_destroy(sp_plan plan);
 
 /*

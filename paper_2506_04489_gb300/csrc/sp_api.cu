@@ -50,11 +50,13 @@ sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what)
         q = p->alloc.alloc(bytes, p->device, p->alloc.ctx);
         if (!q) return sp_fail(SP_ERR_OOM, "allocator returned NULL for %s (%zu bytes)", what, bytes);
     } else {
-        cudaError_t e = cudaMalloc(&q, bytes);
+        // stream-ordered on the plan's private stream, complete before the pointer is used
+        cudaError_t e = cudaMallocAsync(&q, bytes, p->mem_st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->mem_st);
         if (e != cudaSuccess) {
             cudaGetLastError();  // allocation failures are not sticky: clear them
-            return sp_fail(e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA, "cudaMalloc %s (%zu bytes): %s",
-                           what, bytes, cudaGetErrorName(e));
+            return sp_fail(e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA,
+                           "cudaMallocAsync %s (%zu bytes): %s", what, bytes, cudaGetErrorName(e));
         }
     }
     p->alloc_ptr[p->nalloc] = q;
@@ -64,14 +66,23 @@ sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what)
     return SP_OK;
 }
 
-// Release everything the plan owns.  Its work must have completed; called with the plan's
-// device current.
-static void free_plan(sp_plan p)
+// Release everything the plan owns, with the plan's device current.  Device memory of the
+// library's own allocations is freed stream-ordered after the plan's last recorded work
+// (no host wait); a caller's allocator gets its blocks back only after that work has
+// completed (a host wait on the plan's event, not on the device).  Returns the status of
+// that wait.
+static cudaError_t free_plan(sp_plan p)
 {
-    if (!p) return;
-    for (int i = p->nalloc - 1; i >= 0; --i) {
-        if (p->has_alloc) p->alloc.release(p->alloc_ptr[i], p->alloc_bytes[i], p->device, p->alloc.ctx);
-        else cudaFree(p->alloc_ptr[i]);
+    if (!p) return cudaSuccess;
+    cudaError_t err = cudaSuccess;
+    if (p->has_alloc) {
+        if (p->done_recorded) err = cudaEventSynchronize(p->done);
+        for (int i = p->nalloc - 1; i >= 0; --i)
+            p->alloc.release(p->alloc_ptr[i], p->alloc_bytes[i], p->device, p->alloc.ctx);
+    } else if (p->mem_st) {
+        if (p->done_recorded) err = cudaStreamWaitEvent(p->mem_st, p->done, 0);
+        for (int i = p->nalloc - 1; i >= 0; --i) cudaFreeAsync(p->alloc_ptr[i], p->mem_st);
+        cudaStreamDestroy(p->mem_st);  // released once its frees have run
     }
     if (p->ev) {
         for (cudaEvent_t e : *p->ev) cudaEventDestroy(e);
@@ -86,6 +97,7 @@ static void free_plan(sp_plan p)
     }
     free(p->h_gs_a);
     delete p;
+    return err;
 }
 
 static const int kMaxLen = 2048;  // largest padded FFT length 2n per axis
@@ -185,6 +197,12 @@ extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const doubl
         free_plan(p);
         return rc;
     }
+    if (!p->has_alloc &&
+        (rc = sp_cuda_check(cudaStreamCreateWithFlags(&p->mem_st, cudaStreamNonBlocking), "create plan stream"))) {
+        p->mem_st = nullptr;
+        free_plan(p);
+        return rc;
+    }
 #define SP_ALLOC(ptr, bytes)                                                           \
     do {                                                                               \
         if ((rc = sp_plan_alloc(p, (void**)&(ptr), (bytes), #ptr))) {                  \
@@ -222,7 +240,9 @@ extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const doubl
     p->work_bytes = csize * (size_t)max_batch * n[0] * (size_t)p->plane;
     SP_ALLOC(p->d_work, p->work_bytes);
 #undef SP_ALLOC
-    if ((rc = sp_cuda_check(cudaMemset(p->d_status, 0, 256), "clear status word"))) {
+    const cudaError_t ce = p->mem_st ? cudaMemsetAsync(p->d_status, 0, 256, p->mem_st) : cudaMemset(p->d_status, 0, 256);
+    if ((rc = sp_cuda_check(ce == cudaSuccess && p->mem_st ? cudaStreamSynchronize(p->mem_st) : ce,
+                            "clear status word"))) {
         free_plan(p);
         return rc;
     }
@@ -331,10 +351,9 @@ extern "C" sp_status sp_plan_destroy(sp_plan p)
     int cur = -1;
     const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
                           cudaSetDevice(p->device) == cudaSuccess;
-    cudaError_t e = p->done_recorded ? cudaEventSynchronize(p->done) : cudaSuccess;
-    free_plan(p);
+    cudaError_t e = free_plan(p);
     if (switched) cudaSetDevice(cur);
-    return sp_cuda_check(e, "wait for the plan's work before destroy");
+    return sp_cuda_check(e, "order the plan's release after its work");
 }
 
 extern "C" sp_status sp_plan_sync(sp_plan p)

@@ -59,6 +59,10 @@ struct sp_plan_s {
     // through the caller's allocator when one was given, else cudaFree
     sp_allocator alloc;
     bool has_alloc;
+    // without a caller's allocator: stream-ordered allocations (cudaMallocAsync) on this
+    // private stream, freed there (cudaFreeAsync) after the plan's last work, so that
+    // destroy never waits for the device
+    cudaStream_t mem_st;
     int nalloc;
     void* alloc_ptr[32];
     size_t alloc_bytes[32];

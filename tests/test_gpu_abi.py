@@ -61,7 +61,7 @@ def test_torch_allocator_plan_matches_default():
 
 @pytest.mark.parametrize("precision", ["df32", "fp32"])
 def test_solve_host_matches_device_solves(precision):
-    n = (64, 48, 64)
+    n = (64, 32, 96)
     plan = Plan(n, -1.0, 1.0, precision=precision)
     dt = plan.dtype
     ins = [torch.from_numpy(W.gaussian_mixture(n, -1.0, 1.0, s)).to(dt).pin_memory() for s in range(5)]

@@ -35,7 +35,7 @@ def _cases():
     return out
 
 
-_oracle = {}
+_oracle = {}  # every case's density and oracle potential (a few MB each), kept for all precisions
 
 
 def _reference(oracle, n):
@@ -43,7 +43,6 @@ def _reference(oracle, n):
         rng = np.random.default_rng(sum(n) + 17 * n[0])
         rho = rng.standard_normal(n)  # white noise: every wavenumber, every register slot
         _, _, M = oracle.plan_tables(n, LO, HI)
-        _oracle.clear()
         _oracle[n] = (rho, oracle.solve(M, rho))
     return _oracle[n]
 
