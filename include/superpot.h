@@ -275,6 +275,31 @@ sp_status sp_plan_tiles(const sp_plan plan, int* line_tiles, int* z_tile);
  *   sp_graph_launch  -- replay on `stream` (stream-ordered, no host synchronisation).
  *   sp_graph_destroy -- free the graph (NULL accepted).
  */
+/*
+ * sp_plan_set_persistent -- enable != 0: every later solve of the plan (sp_solve,
+ * sp_solve_batched, sp_graph_capture) runs as ONE persistent cooperative kernel launch
+ * (after a 4-byte memset of its barrier counter): each block walks the tiles of the five
+ * passes of Alg. 2 with a stride of the grid size, and a grid-wide barrier separates the
+ * passes.  Results are bitwise those of the default five launches (tiles never change a
+ * line's arithmetic).  The barrier's wait is bounded (2 s): a block that gives up sets
+ * the plan's status word and leaves the kernel, and sp_plan_sync then returns
+ * SP_ERR_TIMEOUT (the results of that solve are then incomplete).  Needs a cubic grid whose
+ * padded length has a compiled plan (2n in {64, 128, 192, 256, 384, 512, 1024}), else
+ * SP_ERR_UNSUPPORTED_SIZE.  enable = 0 returns to five launches.
+ */
+sp_status sp_plan_set_persistent(sp_plan plan, int enable);
+
+/*
+ * sp_plan_barrier_check -- diagnostic of the persistent solve's bounded grid wait:
+ * launches `blocks` co-resident blocks (1 <= blocks <= number of SMs; a cooperative
+ * launch) that each arrive once at a barrier waiting for `expected` arrivals, for at most
+ * `limit_ms` (0 < limit_ms <= 2000) milliseconds.  With expected <= blocks the barrier
+ * completes; with expected > blocks every block gives up after the limit and sets the
+ * plan's status word, which the next sp_plan_sync reports as SP_ERR_TIMEOUT.  Uses the
+ * plan's barrier counter: do not overlap it with the plan's solves.  Stream-ordered.
+ */
+sp_status sp_plan_barrier_check(sp_plan plan, int blocks, int expected, double limit_ms, sp_stream stream);
+
 typedef struct sp_graph_s* sp_graph;
 sp_status sp_graph_capture(sp_plan plan, const void* rho, void* u, int batch, sp_stream stream,
                            sp_graph* out);

@@ -45,6 +45,10 @@ lib.sp_plan_create_ex.argtypes = [ctypes.POINTER(_vp), _ip, _dp, _dp, ctypes.c_i
                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Allocator)]
 lib.sp_solve_host.restype = ctypes.c_int
 lib.sp_solve_host.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp]
+lib.sp_plan_set_persistent.restype = ctypes.c_int
+lib.sp_plan_set_persistent.argtypes = [_vp, ctypes.c_int]
+lib.sp_plan_barrier_check.restype = ctypes.c_int
+lib.sp_plan_barrier_check.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp]
 lib.sp_plan_sync.restype = ctypes.c_int
 lib.sp_plan_sync.argtypes = [_vp]
 lib.sp_kernel_precompute.restype = ctypes.c_int

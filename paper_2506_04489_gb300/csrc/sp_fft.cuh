@@ -19,7 +19,6 @@
 
 #include "sp_common.cuh"
 #include "sp_df32.cuh"
-#include "sp_fx64.cuh"
 
 // ------------------------------------------------------------------ numeric traits
 template <class R> struct Num;
@@ -32,12 +31,6 @@ template <> struct Num<double> {
 template <> struct Num<df32> {
     static SP_HD df32 c(double d) { return df_from_double(d); }
 };
-// Fixed point: the constants of the engine are multipliers (butterfly constants, twiddles)
-// or zero, so they are Q61 multipliers in the pre-split form (sp_fx64.cuh).
-template <> struct Num<fx64> {
-    static SP_HD fx64 c(double d) { return fx_q61(d); }
-};
-
 template <class R> SP_D cpx<R> czero() { return mk(Num<R>::c(0.0), Num<R>::c(0.0)); }
 
 // Twiddle products: the generic forms for float/double; for double-float each part is
@@ -54,27 +47,6 @@ template <> SP_D cpx<df32> tw_mulc<df32>(cpx<df32> a, cpx<df32> w)
     const df32 ar = re_of(a), ai = im_of(a), wr = re_of(w), wi = im_of(w);
     return mk(df_dot_add(ar, wr, ai, wi), df_dot_sub(ai, wr, ar, wi));
 }
-// Fixed point: each part is one split dot product (sp_fx64.cuh); the datum's pieces are
-// shared by both parts, the multiplier's come pre-split.
-template <> SP_D cpx<fx64> tw_mul<fx64>(cpx<fx64> a, cpx<fx64> w)
-{
-    int r1, r0, i1, i0, c1, c0, s1, s0;
-    fx_split(a.re.m, r1, r0);
-    fx_split(a.im.m, i1, i0);
-    fx_pieces(w.re, c1, c0);
-    fx_pieces(w.im, s1, s0);
-    return mk(fx_make(fx_dot(r1, r0, c1, c0, i1, i0, -s1, -s0)), fx_make(fx_dot(r1, r0, s1, s0, i1, i0, c1, c0)));
-}
-template <> SP_D cpx<fx64> tw_mulc<fx64>(cpx<fx64> a, cpx<fx64> w)
-{
-    int r1, r0, i1, i0, c1, c0, s1, s0;
-    fx_split(a.re.m, r1, r0);
-    fx_split(a.im.m, i1, i0);
-    fx_pieces(w.re, c1, c0);
-    fx_pieces(w.im, s1, s0);
-    return mk(fx_make(fx_dot(r1, r0, c1, c0, i1, i0, s1, s0)), fx_make(fx_dot(i1, i0, c1, c0, r1, r0, -s1, -s0)));
-}
-
 // Values written to global memory are renormalised.  Exchanges through shared memory
 // between the stages of one transform keep the pair as the arithmetic left it: sums and
 // products accept a low part of a few ulps of the high part (their error stays a small

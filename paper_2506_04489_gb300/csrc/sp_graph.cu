@@ -6,7 +6,8 @@
 // CTA, never the arithmetic of a line, so results are bitwise the same for every tile.
 //
 // A captured graph replays a (batched) solve on fixed buffers with one host-side launch:
-// five kernel nodes, each over the whole batch.
+// five kernel nodes, each over the whole batch, or (persistent plans) one cooperative
+// kernel node running all five passes with grid barriers between them.
 #include <new>
 
 #include "sp_internal.h"
@@ -133,4 +134,70 @@ extern "C" sp_status sp_graph_destroy(sp_graph g)
     cudaGraphDestroy(g->graph);
     delete g;
     return sp_cuda_check(e, "destroy graph");
+}
+
+extern "C" sp_status sp_plan_set_persistent(sp_plan p, int enable)
+{
+    sp_clear_error();
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (enable && !(p->N[0] == p->N[1] && p->N[1] == p->N[2] && sp_v2_supported(p->N[0])))
+        return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "the persistent solve needs a cubic grid with a compiled padded length");
+    p->persistent = enable != 0;
+    return SP_OK;
+}
+
+// Diagnostic of the bounded grid wait: `blocks` co-resident blocks of 32 threads each
+// arrive once at a barrier that waits for `expected` arrivals.
+__global__ void k_barrier_check(unsigned* count, int* status, unsigned expected, unsigned long long limit_ns)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        unsigned long long t0, t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        const unsigned long long max_polls = limit_ns / 16 + 1024;
+        for (unsigned long long it = 0;; ++it) {
+            if (*(volatile unsigned*)count >= expected) break;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (it >= max_polls || t - t0 > limit_ns) {
+                atomicExch(status, 1);
+                break;
+            }
+            __nanosleep(128);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+extern "C" sp_status sp_plan_barrier_check(sp_plan p, int blocks, int expected, double limit_ms, sp_stream stream)
+{
+    sp_clear_error();
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (sp_status rc = sp_check_device(p)) return rc;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks < 1 || blocks > sms) return sp_fail(SP_ERR_INVALID, "blocks must be in [1, %d] (got %d)", sms, blocks);
+    if (expected < 1) return sp_fail(SP_ERR_INVALID, "expected must be >= 1 (got %d)", expected);
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) return sp_fail(SP_ERR_INVALID, "limit_ms must be in (0, 2000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned* bar = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(p->d_status) + 64);
+    sp_status rc = sp_cuda_check(cudaMemsetAsync(bar, 0, sizeof(unsigned), st), "clear grid barrier");
+    if (rc) return rc;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all blocks co-resident
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const unsigned long long limit_ns = (unsigned long long)(limit_ms * 1e6);
+    if ((rc = sp_cuda_check(cudaLaunchKernelEx(&cfg, k_barrier_check, bar, p->d_status, (unsigned)expected, limit_ns),
+                            "barrier check launch")))
+        return rc;
+    return sp_record_done(p, st);
 }

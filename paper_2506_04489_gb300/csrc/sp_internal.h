@@ -76,6 +76,8 @@ struct sp_plan_s {
     // the line passes per axis, pairs of real lines per CTA of the z passes
     int tile_line[3];
     int tile_z;
+    // solves run as one persistent cooperative launch (sp_plan_set_persistent)
+    bool persistent;
     // pass timing (diagnostic): events recorded between passes while timing is on.  The
     // events are a pool kept for the plan's life: ev_used of them hold the current record
     // ((npass + 1) per recorded solve); the pool grows only when a record outruns it.
@@ -123,6 +125,9 @@ bool sp_v2_supported(int N);
 #define SP_TW_STAGED_MAX 4096
 sp_status sp_v2_stage_twiddles_df(sp_plan p, cudaStream_t st);
 sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st);
+sp_status sp_v2_persistent_f32(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st, bool mixed);
+sp_status sp_v2_persistent_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
+sp_status sp_v2_persistent_df(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
 float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed);
 float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
 float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);

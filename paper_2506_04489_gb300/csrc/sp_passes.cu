@@ -373,6 +373,14 @@ bool sp_v2_supported(int N)
 
 sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
 {
+    if (p->persistent) {  // one cooperative launch for all passes (sp_plan_set_persistent)
+        switch (p->prec) {
+            case SP_FP64: return sp_v2_persistent_f64(p, rho, u, batch, st);
+            case SP_FP32: return sp_v2_persistent_f32(p, rho, u, batch, st, false);
+            case SP_MIXED: return sp_v2_persistent_f32(p, rho, u, batch, st, true);
+            case SP_DF32: return sp_v2_persistent_df(p, rho, u, batch, st);
+        }
+    }
     // register-resident passes where every axis length has a compiled plan
     sp_status rc = SP_ERR_UNSUPPORTED_SIZE;
     switch (p->prec) {

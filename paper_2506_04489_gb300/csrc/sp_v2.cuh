@@ -111,9 +111,11 @@ template <class R, int N, int LGB> constexpr int line_threads()
 }
 template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
 
+// One tile of a line pass: B columns (c = cb B + b) of outer index o, right-hand side
+// `batch`; all threads of the block take part.  `smraw` is the pass's dynamic shared
+// memory (staged twiddles where they live in shared memory, then the exchange buffers).
 template <class R, int N, int MODE, int LGB>
-__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<R, N, line_threads<R, N, LGB>()>() : 1)
-    k2_line(LArgs a)
+SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smraw)
 {
     constexpr int E = PlanOf<R, N>::E, T = N / E;
     constexpr int R0 = PlanOf<R, N>::R[0];
@@ -121,7 +123,6 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
     const int lgB = LGB >= 0 ? LGB : a.lgB, B = 1 << lgB;
     const int BUF = Lay::size(N, B);
     const bool DB = two_buffers(sizeof(cpx<R>) * BUF, pass_tw_bytes<R, N>());
-    extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
     cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
         if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws_s, twg, tid, blockDim.x);
         if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws_s, twg, tid, blockDim.x);
     }
-    const int o = blockIdx.y, c = blockIdx.x * B + b, batch = blockIdx.z;
+    const int c = cb * B + b;
     const bool cv = c < a.ncol;
     const cpx<R>* in = static_cast<const cpx<R>*>(a.in) + batch * a.in_bs + o * a.in_os + c;
     cpx<R>* out = static_cast<cpx<R>*>(a.out) + batch * a.out_bs + o * a.out_os + c;
@@ -198,6 +199,14 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_bloc
         for (int j = 0; j < E; ++j)
             if ((j % R0) < R0 / 2 && cv) out[last_element<R, N, true>(t, j) * a.out_es] = norm(v[j]);
     }
+}
+
+template <class R, int N, int MODE, int LGB>
+__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<R, N, line_threads<R, N, LGB>()>() : 1)
+    k2_line(LArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    line_tile<R, N, MODE, LGB>(a, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
 }
 
 // ------------------------------------------------------------------ pipelined line passes
@@ -397,14 +406,14 @@ template <class R, int N> SP_HD bool z_two_buffers(int B)
     return two_buffers(sizeof(cpx<R>) * z_buf<R, N>(B), pass_tw_bytes<R, N, ZKey<R>>());
 }
 
+// One tile of the z forward pass: a.B pairs of real lines starting at pair block `blk`,
+// right-hand side `batch`.
 template <class R, class Tio, int N>
-__global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
-                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
+SP_D void zf_tile(const ZArgs2& a, int blk, int batch, unsigned char* smraw)
 {
     constexpr int E = PlanOf<ZKey<R>, N>::E, T = N / E;
     const int B = a.B;
     constexpr int R0 = PlanOf<ZKey<R>, N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N, ZKey<R>>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
@@ -412,9 +421,9 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
     const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
     if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, false, ZKey<R>>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
-    const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
-    const Tio* rho = static_cast<const Tio*>(a.rho) + blockIdx.y * a.io_bs;
-    cpx<R>* W = static_cast<cpx<R>*>(a.W) + blockIdx.y * a.w_bs;
+    const long long l0 = 2 * ((long long)blk * B + b), l1 = l0 + 1;
+    const Tio* rho = static_cast<const Tio*>(a.rho) + batch * a.io_bs;
+    cpx<R>* W = static_cast<cpx<R>*>(a.W) + batch * a.w_bs;
     const LayLine<N> lay{b * LayLine<N>::LD};
     cpx<R> v[E];
 #pragma unroll
@@ -446,12 +455,19 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
 
 template <class R, class Tio, int N>
 __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
-                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
+                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    zf_tile<R, Tio, N>(a, blockIdx.x, blockIdx.y, smraw);
+}
+
+// One tile of the z inverse pass (pairs of real output lines), as zf_tile.
+template <class R, class Tio, int N>
+SP_D void zi_tile(const ZArgs2& a, int blk, int batch, unsigned char* smraw)
 {
     constexpr int E = PlanOf<ZKey<R>, N>::E, T = N / E;
     const int B = a.B;
     constexpr int R0 = PlanOf<ZKey<R>, N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
     cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N, ZKey<R>>() / sizeof(cpx<R>);
     cpx<R>* sm1 = z_two_buffers<R, N>(B) ? sm0 + z_buf<R, N>(B) : sm0;
@@ -459,9 +475,9 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
     const cpx<R>* tws = tw_global<R, N>() ? static_cast<const cpx<R>*>(a.tw) + N : tws_s;
     if constexpr (!tw_global<R, N>()) fill_stage_twiddles<R, N, true, ZKey<R>>(tws_s, static_cast<const cpx<R>*>(a.tw), tid, blockDim.x);
     const int n2 = a.n2;
-    const long long l0 = 2 * ((long long)blockIdx.x * B + b), l1 = l0 + 1;
-    Tio* u = static_cast<Tio*>(a.u) + blockIdx.y * a.io_bs;
-    const cpx<R>* W = static_cast<const cpx<R>*>(a.W) + blockIdx.y * a.w_bs;
+    const long long l0 = 2 * ((long long)blk * B + b), l1 = l0 + 1;
+    Tio* u = static_cast<Tio*>(a.u) + batch * a.io_bs;
+    const cpx<R>* W = static_cast<const cpx<R>*>(a.W) + batch * a.w_bs;
     const LayLine<N> lay{b * LayLine<N>::LD};
     // Z_k = Xa_k + i Xb_k from the Hermitian halves (DC and Nyquist take real parts)
     const long long r0 = w_row(a, l0), r1 = w_row(a, l1 < a.lines ? l1 : l0);
@@ -487,6 +503,14 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
             if (l1 < a.lines) u[l1 * n2 + z] = from_r<R, Tio>(im_of(v[j]));
         }
     }
+}
+
+template <class R, class Tio, int N>
+__global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
+                                  min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    zi_tile<R, Tio, N>(a, blockIdx.x, blockIdx.y, smraw);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -780,6 +804,237 @@ float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return ms;
+}
+
+// ------------------------------------------------------------------ persistent solve
+// All five passes of a (batched) solve in one cooperative launch: every block walks the
+// tiles of a pass with a stride of the grid size, then waits at a grid barrier until every
+// block has finished that pass (the next pass reads what all of them wrote).  The barrier
+// is a counter the host clears before the launch; the wait is bounded (grid_wait), and a
+// block that gives up records SP_ERR_TIMEOUT's cause in the plan's status word and leaves
+// the kernel without running the remaining passes.  One block shape serves every pass:
+// THREADS threads hold B = THREADS / T line columns (line passes) or THREADS / T_z pairs
+// of real lines (z passes).
+SP_D unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Arrive at barrier number `k` (1, 2, ...) of this launch and wait, at most `limit_ns`
+// nanoseconds (and a bounded number of polls), until all `nblocks` blocks have arrived.
+// Returns false, after setting *status, when the wait gave up.  All threads call it.
+SP_D bool grid_wait(unsigned* count, int* status, unsigned k, unsigned nblocks, unsigned long long limit_ns)
+{
+    __shared__ int ok;
+    __syncthreads();  // the block's writes of this pass precede the arrival
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned target = k * nblocks;
+        const unsigned long long t0 = global_ns();
+        const unsigned long long max_polls = limit_ns / 16 + 1024;
+        for (unsigned long long it = 0;; ++it) {
+            const unsigned v = *(volatile unsigned*)count;
+            if (v >= target) break;
+            if (it >= max_polls || ((it & 31) == 0 && global_ns() - t0 > limit_ns)) {
+                atomicExch(status, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(128);
+        }
+        __threadfence();  // the other blocks' writes are visible after the wait
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct PersistArgs {
+    ZArgs2 z;           // z.B pairs per tile
+    LArgs y, x;         // B columns per tile (compile-time in the kernel)
+    int batch;
+    int z_tiles, y_ncb, y_outer, x_ncb, x_outer;  // per right-hand side
+    unsigned* bar;      // barrier counter, cleared before the launch
+    int* status;
+    unsigned long long limit_ns;
+};
+
+template <class R, int N> constexpr int persist_threads()
+{
+    constexpr int T = N / PlanOf<R, N>::E;
+    return T * lanes_b_max<R, N>() < 256 ? T * lanes_b_max<R, N>() : 256;
+}
+template <class R, int N> constexpr int persist_lgb()
+{
+    constexpr int B = persist_threads<R, N>() / (N / PlanOf<R, N>::E);
+    return B >= 16 ? 4 : (B >= 8 ? 3 : (B >= 4 ? 2 : (B >= 2 ? 1 : 0)));
+}
+template <class R, int N> constexpr int persist_bz() { return persist_threads<R, N>() / (N / PlanOf<ZKey<R>, N>::E); }
+template <class R, int N> constexpr bool persist_ok()
+{
+    constexpr int TH = persist_threads<R, N>(), T = N / PlanOf<R, N>::E, Tz = N / PlanOf<ZKey<R>, N>::E;
+    return TH % T == 0 && (1 << persist_lgb<R, N>()) * T == TH && TH % Tz == 0 && persist_bz<R, N>() >= 1 &&
+           pairs_max<N>() % persist_bz<R, N>() == 0;
+}
+template <class R, int N> constexpr size_t persist_smem()
+{
+    constexpr int B = 1 << persist_lgb<R, N>();
+    constexpr size_t lbuf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
+    constexpr size_t ltw = pass_tw_bytes<R, N>();
+    constexpr size_t line = ltw + (two_buffers(lbuf, ltw) ? 2 : 1) * lbuf;
+    constexpr size_t zbuf = sizeof(cpx<R>) * (size_t)persist_bz<R, N>() * LayLine<N>::LD;
+    constexpr size_t ztw = pass_tw_bytes<R, N, ZKey<R>>();
+    constexpr size_t zs = ztw + (two_buffers(zbuf, ztw) ? 2 : 1) * zbuf;
+    return line > zs ? line : zs;
+}
+
+template <class R, class Tio, int N>
+__global__ void __launch_bounds__(persist_threads<R, N>(), 1) k_persist(PersistArgs pa)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int LGB = persist_lgb<R, N>();
+    const unsigned nb = gridDim.x;
+    // pass 1: z forward
+    const int zt = pa.batch * pa.z_tiles;
+    for (int tile = blockIdx.x; tile < zt; tile += gridDim.x) {
+        zf_tile<R, Tio, N>(pa.z, tile % pa.z_tiles, tile / pa.z_tiles, smraw);
+        __syncthreads();
+    }
+    if (!grid_wait(pa.bar, pa.status, 1, nb, pa.limit_ns)) return;
+    // pass 2: y forward; pass 3: x forward * M * x inverse; pass 4: y inverse
+    const int yt = pa.batch * pa.y_outer * pa.y_ncb;
+    for (int tile = blockIdx.x; tile < yt; tile += gridDim.x) {
+        const int r = tile / pa.y_ncb;
+        line_tile<R, N, FWD, LGB>(pa.y, tile % pa.y_ncb, r % pa.y_outer, r / pa.y_outer, smraw);
+        __syncthreads();
+    }
+    if (!grid_wait(pa.bar, pa.status, 2, nb, pa.limit_ns)) return;
+    const int xt = pa.batch * pa.x_outer * pa.x_ncb;
+    for (int tile = blockIdx.x; tile < xt; tile += gridDim.x) {
+        const int r = tile / pa.x_ncb;
+        line_tile<R, N, XMUL, LGB>(pa.x, tile % pa.x_ncb, r % pa.x_outer, r / pa.x_outer, smraw);
+        __syncthreads();
+    }
+    if (!grid_wait(pa.bar, pa.status, 3, nb, pa.limit_ns)) return;
+    for (int tile = blockIdx.x; tile < yt; tile += gridDim.x) {
+        const int r = tile / pa.y_ncb;
+        line_tile<R, N, INV, LGB>(pa.y, tile % pa.y_ncb, r % pa.y_outer, r / pa.y_outer, smraw);
+        __syncthreads();
+    }
+    if (!grid_wait(pa.bar, pa.status, 4, nb, pa.limit_ns)) return;
+    // pass 5: z inverse
+    for (int tile = blockIdx.x; tile < zt; tile += gridDim.x) {
+        zi_tile<R, Tio, N>(pa.z, tile % pa.z_tiles, tile / pa.z_tiles, smraw);
+        __syncthreads();
+    }
+}
+
+// Bounded wait of the persistent solve's barrier: a wait shorter than any pass would
+// report a timeout for a healthy solve.
+constexpr unsigned long long kPersistLimitNs = 2000000000ull;  // 2 s
+
+template <class R, class Tio> struct PersistRun {
+    sp_plan p;
+    const void* rho;
+    void* u;
+    int batch;
+    cudaStream_t st;
+    template <int N> sp_status run()
+    {
+        if constexpr (!persist_ok<R, N>()) {
+            return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no persistent solve for padded length %d in this precision", N);
+        } else {
+            constexpr int TH = persist_threads<R, N>(), B = 1 << persist_lgb<R, N>();
+            constexpr size_t smem = persist_smem<R, N>();
+            PersistArgs pa = {};
+            ZArgs2& z = pa.z;
+            z.rho = rho;
+            z.u = u;
+            z.W = p->d_work;
+            z.n1 = p->n[1];
+            z.n2 = p->n[2];
+            z.lines = (long long)p->n[0] * p->n[1];
+            z.plane = p->plane;
+            z.ldz = p->ldz;
+            z.io_bs = (long long)p->n[0] * p->n[1] * p->n[2];
+            z.w_bs = (long long)p->n[0] * p->plane;
+            z.tw = Tabs<R>::tw(p, 2);
+            z.B = persist_bz<R, N>();
+            LArgs& y = pa.y;
+            y.in = y.out = p->d_work;
+            y.in_os = y.out_os = p->plane;
+            y.in_es = y.out_es = p->ldz;
+            y.in_bs = y.out_bs = (long long)p->n[0] * p->plane;
+            y.ncol = p->n[2] + 1;
+            y.in_ld = p->ldz;
+            y.tw = Tabs<R>::tw(p, 1);
+            y.B = B;
+            y.lgB = persist_lgb<R, N>();
+            pa.x = y;
+            LArgs& x = pa.x;
+            x.in_os = x.out_os = p->ldz;
+            x.in_es = x.out_es = p->plane;
+            x.tw = Tabs<R>::tw(p, 0);
+            x.M = Tabs<R>::M(p);
+            x.No = p->N[1];
+            x.nh_line = p->n[0];
+            x.ldzM = p->ldz;
+            pa.batch = batch;
+            pa.z_tiles = (int)(((z.lines + 1) / 2 + z.B - 1) / z.B);
+            pa.y_ncb = pa.x_ncb = (y.ncol + B - 1) / B;
+            pa.y_outer = p->n[0];
+            pa.x_outer = p->N[1];
+            pa.bar = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(p->d_status) + 64);
+            pa.status = p->d_status;
+            pa.limit_ns = kPersistLimitNs;
+            sp_status rc;
+            if ((rc = smem_attr<k_persist<R, Tio, N>>(smem))) return rc;
+            static std::atomic<int> per_sm_cached{0};
+            int per_sm = per_sm_cached.load(std::memory_order_relaxed);
+            if (!per_sm) {
+                if ((rc = sp_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<R, Tio, N>, TH,
+                                                                                      smem), "persistent occupancy")))
+                    return rc;
+                if (per_sm < 1) return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "persistent solve: no block fits an SM");
+                per_sm_cached.store(per_sm, std::memory_order_relaxed);
+            }
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const long long most = (long long)batch * (pa.x_outer * pa.x_ncb > 2 * pa.z_tiles ? pa.x_outer * pa.x_ncb : pa.z_tiles);
+            const int nblocks = (int)(most < (long long)per_sm * sms ? most : (long long)per_sm * sms);
+            if ((rc = sp_cuda_check(cudaMemsetAsync(pa.bar, 0, sizeof(unsigned), st), "clear grid barrier"))) return rc;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)nblocks);
+            cfg.blockDim = dim3((unsigned)TH);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            return sp_cuda_check(cudaLaunchKernelEx(&cfg, k_persist<R, Tio, N>, pa), "persistent solve launch");
+        }
+    }
+};
+
+// The whole (batched) solve as one persistent cooperative launch, for cubic grids whose
+// padded length has a compiled plan.
+template <class R, class Tio>
+sp_status solve_persistent(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
+{
+    if (!(p->N[0] == p->N[1] && p->N[1] == p->N[2]) || !len_ok(p->N[0]))
+        return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "the persistent solve needs a cubic grid with a compiled padded length");
+    p->npass = 1;
+    p->pass_name[0] = "persistent";
+    sp_status rc;
+    if ((rc = sp_mark(p, st))) return rc;
+    if ((rc = with_len(p->N[0], PersistRun<R, Tio>{p, rho, u, batch, st}))) return rc;
+    return sp_mark(p, st);
 }
 
 // Forward half only (diagnostic): spectrum[kx][ky][kz], kz <= n2 dense.

@@ -28,3 +28,8 @@ float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cu
 {
     return v2::time_pass<df32, double>(p, pass, tile, batch, iters, st);
 }
+
+sp_status sp_v2_persistent_df(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
+{
+    return v2::solve_persistent<df32, double>(p, rho, u, batch, st);
+}

@@ -28,3 +28,9 @@ sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st)
 {
     return v2::stage_twiddles<float>(p, st);
 }
+
+sp_status sp_v2_persistent_f32(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st, bool mixed)
+{
+    return mixed ? v2::solve_persistent<float, double>(p, rho, u, batch, st)
+                 : v2::solve_persistent<float, float>(p, rho, u, batch, st);
+}

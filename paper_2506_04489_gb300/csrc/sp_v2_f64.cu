@@ -22,3 +22,8 @@ float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, c
 {
     return v2::time_pass<double, double>(p, pass, tile, batch, iters, st);
 }
+
+sp_status sp_v2_persistent_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
+{
+    return v2::solve_persistent<double, double>(p, rho, u, batch, st);
+}

@@ -192,6 +192,15 @@ class Plan:
         self._N.check(self._N.lib.sp_plan_tiles(self._h, line, ctypes.byref(z)), "sp_plan_tiles")
         return {"line": tuple(line), "z": z.value}
 
+    def set_persistent(self, enable: bool = True) -> None:
+        """Run solves as one persistent cooperative launch (sp_plan_set_persistent)."""
+        self._N.check(self._N.lib.sp_plan_set_persistent(self._h, int(bool(enable))), "sp_plan_set_persistent")
+
+    def barrier_check(self, blocks: int, expected: int, limit_ms: float = 50.0, stream=None) -> None:
+        """Diagnostic of the bounded grid wait (sp_plan_barrier_check); see sync()."""
+        self._N.check(self._N.lib.sp_plan_barrier_check(self._h, int(blocks), int(expected), float(limit_ms),
+                                                        _stream_handle(stream)), "sp_plan_barrier_check")
+
     def capture(self, rho, out, stream):
         """CUDA graph of solve_batched(rho, out) on these buffers; replay with Graph.launch."""
         self._check_io(rho, True)
