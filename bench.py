@@ -627,7 +627,7 @@ def run_configs():
                              "unit": "grid pts/s"}
                 graph.close()
             best = min(rec, key=lambda k: rec[k]["ms_per_batch"])
-            c4[prec] = dict(rec[best], launch=best, tiles=plan.tiles(), modes=rec)
+            c4[prec] = dict(rec[best], launch=best, launch_config=plan.launch_config(), modes=rec)
             plan.close()
             del rho, u
             torch.cuda.empty_cache()
@@ -653,7 +653,7 @@ def run_ours(args, world, rank, local):
     sampler = ClockSampler(local)
     for prec in ("fp64", "df32", "fp32"):
         plan = Plan(n, BOX[0], BOX[1], precision=prec)
-        plan.autotune(1)  # the library's own tile autotuner (setup, not timed)
+        launch_config = plan.autotune(1)  # the library's own autotuner (tiles, radix plans; setup, not timed)
         dt = plan.dtype
         base = torch.from_numpy(rho_np).to(dev, dtype=dt)
         rhos = [base.clone() for _ in range(3)]
@@ -680,6 +680,7 @@ def run_ours(args, world, rank, local):
             m_octant = plan.tables(0)["M"]  # multiplier / Ntilde, for the cuFFT comparison
         else:
             rel_dev = float((u_dev - ref_u).abs().max() / ref_u.abs().max())
+        roof["launch_config"] = launch_config
         results[prec] = {"value": value, "ms_per_step": ms_step, "roofline": roof,
                          "max_rel_dev_from_fp64": rel_dev,
                          "hbm_roofline": {"frac": hbm_frac, "bytes_per_point": minimal_bytes_per_point(prec),
@@ -774,7 +775,7 @@ def run_profile_case(args):
         plan.solve(rho, out)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": {"n": n, "precision": prec, "solves": k, "tiles": plan.tiles()}}))
+    print(json.dumps({"profile_case": {"n": n, "precision": prec, "solves": k, "launch_config": plan.launch_config()}}))
     plan.close()
     return 0
 

@@ -252,17 +252,45 @@ int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char
 /*
  * Batched execution (configurations with many right-hand sides of one size).
  *
- * sp_plan_autotune -- choose the CTA tiles of the solve passes for `batch` right-hand
- *   sides (1 <= batch <= max_batch) by timing every candidate tile of each pass on the
- *   plan's workspace (host synchronising; overwrites the workspace).  Tiles decide which
- *   lines share a CTA, never the arithmetic of a line: results are bitwise identical for
- *   any tile.  A no-op for grids without compiled register-resident passes.
+ * sp_plan_autotune -- choose the CTA tiles of the solve passes, and the radix plan of the
+ *   line passes, for `batch` right-hand sides (1 <= batch <= max_batch) by timing every
+ *   candidate of each pass on the plan's workspace at that batch (host synchronising;
+ *   overwrites the workspace).  Tiles decide which lines share a CTA, never the
+ *   arithmetic of a line: results are bitwise identical for any tile.  Where a type and
+ *   length has an alternative radix plan (FP32 and mixed at 2n = 256, 512, 1024:
+ *   eight- or sixteen-value plans beside the built-in 16-16, 32-16, 32-32; double-float
+ *   at 256: 16-16 beside 8-8-4), the line passes of each axis also time it; another plan
+ *   rounds differently, so results then agree to the precision's tolerance, not bitwise.
+ *   A no-op for grids without compiled register-resident passes.
  * sp_plan_tiles -- the tiles in use: line_tiles[3] (columns per CTA of the y and x line
  *   passes, by axis; 0 = default) and *z_tile (pairs of real lines per CTA of the z
  *   passes).  Either pointer may be NULL.
  */
 sp_status sp_plan_autotune(sp_plan plan, int batch, sp_stream stream);
 sp_status sp_plan_tiles(const sp_plan plan, int* line_tiles, int* z_tile);
+
+/*
+ * sp_plan_launch_config -- the launch configuration in use (what sp_plan_autotune chose):
+ *   line_tiles[3], *z_tile : as sp_plan_tiles;
+ *   line_plan[3]           : radix plan of the line passes per axis (index 0: the x pass,
+ *                            1: the y passes; 0 built-in, 1 the alternative plan);
+ *   radices[24]            : radices[8 ax + s] = radix of stage s of the forward transform
+ *                            of the passes along axis ax (x pass, y passes, z passes), 0
+ *                            after the last stage.
+ * Any pointer may be NULL.
+ */
+sp_status sp_plan_launch_config(const sp_plan plan, int* line_tiles, int* z_tile, int* line_plan, int* radices);
+
+/*
+ * sp_plan_set_launch_config -- set a launch configuration instead of tuning one (for
+ * example one that sp_plan_autotune chose earlier and the caller saved): line_tiles[3]
+ * and z_tile as sp_plan_tiles reports them (0 = built-in), line_plan[3] as
+ * sp_plan_launch_config reports it (index 2 must be 0).  A NULL pointer leaves that part
+ * unchanged.  A radix plan that does not exist for the type and length is
+ * SP_ERR_UNSUPPORTED_SIZE; a tile outside a pass's range fails at the next solve with
+ * SP_ERR_INVALID.
+ */
+sp_status sp_plan_set_launch_config(sp_plan plan, const int* line_tiles, int z_tile, const int* line_plan);
 
 /*
  * CUDA-graph capture of a (batched) solve on fixed buffers, replayed with one launch.

@@ -114,6 +114,25 @@ template <class R, int N> struct PlanOf<ZKey<R>, N> : PlanOf<R, N> {};
 template <> struct PlanOf<ZKey<float>, 512> : FFTPlan<512> {};
 template <> struct PlanOf<ZKey<float>, 1024> : Plan1024Radix16 {};
 
+// Alternative radix plans of the line passes, which the autotuner times against the
+// built-in plan of the same type and length (LineKey<R, 1>; LineKey<R, 0> is the built-in
+// plan PlanOf<R, N>).  Each has its own staged twiddle table in global memory, after the
+// built-in plan's.
+template <class R, int N> struct AltPlan {
+    static constexpr bool exists = false;
+};
+// FP32: the eight-value plans (two exchanges a transform instead of one, about a third of
+// the registers, so twice the resident warps)
+template <> struct AltPlan<float, 256> : FFTPlan<256> { static constexpr bool exists = true; };
+template <> struct AltPlan<float, 512> : FFTPlan<512> { static constexpr bool exists = true; };
+template <> struct AltPlan<float, 1024> : Plan1024Radix16 { static constexpr bool exists = true; };
+// double-float: sixteen values a thread at 256 (one exchange a transform instead of two)
+template <> struct AltPlan<df32, 256> : Plan256Radix16 { static constexpr bool exists = true; };
+template <class R, int V> struct LineKey {};
+template <class R, int N> struct PlanOf<LineKey<R, 0>, N> : PlanOf<R, N> {};
+template <class R, int N> struct PlanOf<LineKey<R, 1>, N> : AltPlan<R, N> {};
+template <class K> struct KeyVariant { static constexpr int v = 0; };
+template <class R, int V> struct KeyVariant<LineKey<R, V>> { static constexpr int v = V; };
 // radix of stage s of the forward (INV = false) or inverse (reversed) transform
 template <class R, int N, bool INV> constexpr int radix_at(int s)
 {

@@ -18,13 +18,13 @@ struct sp_graph_s {
     sp_plan plan;  // its completion event is recorded after every replay
 };
 
-static float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
+static float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, int variant)
 {
     switch (p->prec) {
-        case SP_FP64: return sp_v2_time_pass_f64(p, pass, tile, batch, iters, st);
-        case SP_FP32: return sp_v2_time_pass_f32(p, pass, tile, batch, iters, st, false);
-        case SP_MIXED: return sp_v2_time_pass_f32(p, pass, tile, batch, iters, st, true);
-        case SP_DF32: return sp_v2_time_pass_df(p, pass, tile, batch, iters, st);
+        case SP_FP64: return sp_v2_time_pass_f64(p, pass, tile, batch, iters, st, variant);
+        case SP_FP32: return sp_v2_time_pass_f32(p, pass, tile, batch, iters, st, false, variant);
+        case SP_MIXED: return sp_v2_time_pass_f32(p, pass, tile, batch, iters, st, true, variant);
+        case SP_DF32: return sp_v2_time_pass_df(p, pass, tile, batch, iters, st, variant);
     }
     return -1.f;
 }
@@ -41,15 +41,19 @@ extern "C" sp_status sp_plan_autotune(sp_plan p, int batch, sp_stream stream)
         if (!sp_v2_supported(p->N[ax])) return SP_OK;  // first-generation passes: nothing to tune
     cudaStream_t st = (cudaStream_t)stream;
     const int candidates[6] = {1, 2, 4, 8, 16, 32};
-    int best_tile[3] = {0, 0, 0};
+    int best_tile[3] = {0, 0, 0}, best_variant[3] = {0, 0, 0};
     for (int pass = 0; pass < 3; ++pass) {
         float best = -1.f;
-        for (int c = 0; c < 6; ++c) {
-            float ms = time_pass(p, pass, candidates[c], batch, 5, st);
-            sp_clear_error();  // tiles beyond a pass's limit report an error: skip them
-            if (ms > 0.f && (best < 0.f || ms < best)) {
-                best = ms;
-                best_tile[pass] = candidates[c];
+        // the line passes (1: y, 2: x) also try the alternative radix plan of their length
+        for (int variant = 0; variant < (pass == 0 ? 1 : 2); ++variant) {
+            for (int c = 0; c < 6; ++c) {
+                float ms = time_pass(p, pass, candidates[c], batch, 5, st, variant);
+                sp_clear_error();  // tiles beyond a pass's limit, and absent plans, report an error: skip them
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_tile[pass] = candidates[c];
+                    best_variant[pass] = variant;
+                }
             }
         }
         if (best < 0.f) return sp_fail(SP_ERR_CUDA, "autotune: no tile of pass %d ran", pass);
@@ -57,7 +61,70 @@ extern "C" sp_status sp_plan_autotune(sp_plan p, int batch, sp_stream stream)
     p->tile_z = best_tile[0];
     p->tile_line[1] = best_tile[1];
     p->tile_line[0] = best_tile[2];
+    p->line_variant[1] = best_variant[1];
+    p->line_variant[0] = best_variant[2];
     return sp_cuda_check(cudaStreamSynchronize(st), "autotune");
+}
+
+extern "C" sp_status sp_plan_launch_config(const sp_plan p, int* line_tiles, int* z_tile, int* line_plan, int* radices)
+{
+    sp_clear_error();
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (line_tiles)
+        for (int ax = 0; ax < 3; ++ax) line_tiles[ax] = p->tile_line[ax];
+    if (z_tile) *z_tile = p->tile_z;
+    if (line_plan)
+        for (int ax = 0; ax < 3; ++ax) line_plan[ax] = p->line_variant[ax];
+    if (radices) {
+        for (int i = 0; i < 24; ++i) radices[i] = 0;
+        bool v2 = true;
+        for (int ax = 0; ax < 3; ++ax) v2 = v2 && sp_v2_supported(p->N[ax]);
+        if (v2) {
+            sp_status rc = SP_OK;
+            switch (p->prec) {
+                case SP_FP64: rc = sp_v2_radices_f64(p, radices); break;
+                case SP_FP32:
+                case SP_MIXED: rc = sp_v2_radices_f32(p, radices); break;
+                case SP_DF32: rc = sp_v2_radices_df(p, radices); break;
+            }
+            if (rc) return rc;
+        } else {  // first-generation passes: the runtime stage plans
+            for (int ax = 0; ax < 3; ++ax)
+                for (int s = 0; s < p->rp[ax].nst && s < 8; ++s) radices[8 * ax + s] = p->rp[ax].r[s];
+        }
+    }
+    return SP_OK;
+}
+
+extern "C" sp_status sp_plan_set_launch_config(sp_plan p, const int* line_tiles, int z_tile, const int* line_plan)
+{
+    sp_clear_error();
+    if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (z_tile < 0) return sp_fail(SP_ERR_INVALID, "z_tile must be >= 0 (got %d)", z_tile);
+    if (line_tiles)
+        for (int ax = 0; ax < 3; ++ax)
+            if (line_tiles[ax] < 0) return sp_fail(SP_ERR_INVALID, "line_tiles[%d] must be >= 0", ax);
+    if (line_plan) {
+        if (line_plan[2] != 0) return sp_fail(SP_ERR_INVALID, "line_plan[2] must be 0 (the z passes have no line plan)");
+        for (int ax = 0; ax < 2; ++ax) {
+            if (line_plan[ax] != 0 && line_plan[ax] != 1)
+                return sp_fail(SP_ERR_INVALID, "line_plan[%d] must be 0 or 1", ax);
+            if (line_plan[ax] == 1) {
+                const bool has = (p->prec == SP_FP32 || p->prec == SP_MIXED) ? sp_v2_has_alt_f32(p->N[ax])
+                                 : p->prec == SP_DF32                         ? sp_v2_has_alt_df(p->N[ax])
+                                                                              : false;
+                if (!has)
+                    return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no alternative radix plan for axis %d (2n = %d) in this precision",
+                                   ax, p->N[ax]);
+            }
+        }
+    }
+    if (line_tiles)
+        for (int ax = 0; ax < 3; ++ax) p->tile_line[ax] = line_tiles[ax];
+    p->tile_z = z_tile;
+    if (line_plan)
+        for (int ax = 0; ax < 2; ++ax) p->line_variant[ax] = line_plan[ax];
+    return SP_OK;
 }
 
 extern "C" sp_status sp_plan_tiles(const sp_plan p, int* line_tiles, int* z_tile)

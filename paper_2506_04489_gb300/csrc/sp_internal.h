@@ -76,6 +76,9 @@ struct sp_plan_s {
     // the line passes per axis, pairs of real lines per CTA of the z passes
     int tile_line[3];
     int tile_z;
+    // radix plan of the line passes per axis (0: built-in, 1: the alternative plan of the
+    // type and length), chosen by the autotuner
+    int line_variant[3];
     // solves run as one persistent cooperative launch (sp_plan_set_persistent)
     bool persistent;
     // pass timing (diagnostic): events recorded between passes while timing is on.  The
@@ -122,15 +125,22 @@ bool sp_v2_supported(int N);
 // Double-float and FP32 plans keep, after the N base twiddles of an axis, the per-stage
 // twiddle tables that their passes read from global memory; room for this many entries
 // is reserved.
-#define SP_TW_STAGED_MAX 4096
+#define SP_TW_STAGED_MAX 8192
 sp_status sp_v2_stage_twiddles_df(sp_plan p, cudaStream_t st);
 sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st);
 sp_status sp_v2_persistent_f32(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st, bool mixed);
 sp_status sp_v2_persistent_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
 sp_status sp_v2_persistent_df(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);
-float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed);
-float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
-float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st);
+float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed, int variant);
+float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, int variant);
+float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, int variant);
+// radices of the register-resident passes in use: out[8 ax + s], ax = x, y, z passes
+// whether the type has an alternative radix plan for the line passes at padded length N
+bool sp_v2_has_alt_f32(int N);
+bool sp_v2_has_alt_df(int N);
+sp_status sp_v2_radices_f32(sp_plan p, int* out);
+sp_status sp_v2_radices_f64(sp_plan p, int* out);
+sp_status sp_v2_radices_df(sp_plan p, int* out);
 
 // Solve passes (sp_passes.cu).
 sp_status sp_run_solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st);

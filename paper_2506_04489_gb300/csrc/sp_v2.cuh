@@ -66,6 +66,13 @@ template <class R, int N> constexpr int tw_entries() { return (tw_stage_size<R, 
 // 20-30 % faster).  The pipelined line kernel keeps its tables in shared memory.
 template <class R, int N> constexpr bool tw_global() { return std::is_same<R, df32>::value || std::is_same<R, float>::value; }
 template <class R, int N, class K = R> constexpr size_t pass_tw_bytes() { return tw_global<R, N>() ? 0 : sizeof(cpx<R>) * tw_entries<K, N>(); }
+
+// Offset of plan key K's staged table after an axis's N base twiddles (entries).
+template <class R, int N, class K> constexpr int tw_key_offset()
+{
+    if constexpr (KeyVariant<K>::v == 1) return tw_entries<R, N>();
+    else return 0;
+}
 constexpr bool two_buffers(size_t buf_bytes, size_t tw_bytes) { return 2 * buf_bytes + tw_bytes <= 100 * 1024; }
 
 // ------------------------------------------------------------------ strided passes
@@ -97,7 +104,7 @@ template <int N> constexpr int lanes_b_default() { return N >= 1024 ? 4 : 8; }
 // Resident CTAs per SM requested from the compiler: 1024 threads per SM (at most 64
 // registers per thread) for the 8-value plans, to hide global-memory latency; the
 // 24-value plans (lengths with a factor 3) keep their registers.
-template <class R, int N, int THREADS> constexpr int min_blocks() { return PlanOf<R, N>::E <= 8 ? 1024 / THREADS : 1; }
+template <class K, int N, int THREADS> constexpr int min_blocks() { return PlanOf<K, N>::E <= 8 ? 1024 / THREADS : 1; }
 
 // LGB >= 0: the tile 2^LGB is a compile-time constant (the default tile); LGB = -1: the
 // tile comes from a.lgB (other tiles chosen by the autotuner).
@@ -105,33 +112,33 @@ template <class R, int N> constexpr int lg_max()
 {
     return lanes_b_max<R, N>() >= 16 ? 4 : (lanes_b_max<R, N>() >= 8 ? 3 : 2);
 }
-template <class R, int N, int LGB> constexpr int line_threads()
+template <class R, int N, int LGB, class K = R> constexpr int line_threads()
 {
-    return (N / PlanOf<R, N>::E) << (LGB >= 0 ? LGB : lg_max<R, N>());
+    return (N / PlanOf<K, N>::E) << (LGB >= 0 ? LGB : lg_max<R, N>());
 }
 template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
 
 // One tile of a line pass: B columns (c = cb B + b) of outer index o, right-hand side
 // `batch`; all threads of the block take part.  `smraw` is the pass's dynamic shared
 // memory (staged twiddles where they live in shared memory, then the exchange buffers).
-template <class R, int N, int MODE, int LGB>
+template <class R, int N, int MODE, int LGB, class K = R>
 SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smraw)
 {
-    constexpr int E = PlanOf<R, N>::E, T = N / E;
-    constexpr int R0 = PlanOf<R, N>::R[0];
+    constexpr int E = PlanOf<K, N>::E, T = N / E;
+    constexpr int R0 = PlanOf<K, N>::R[0];
     using Lay = LayStrided<R>;
     const int lgB = LGB >= 0 ? LGB : a.lgB, B = 1 << lgB;
     const int BUF = Lay::size(N, B);
-    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, pass_tw_bytes<R, N>());
+    const bool DB = two_buffers(sizeof(cpx<R>) * BUF, pass_tw_bytes<R, N, K>());
     cpx<R>* tws_s = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N>() / sizeof(cpx<R>);
+    cpx<R>* sm0 = tws_s + pass_tw_bytes<R, N, K>() / sizeof(cpx<R>);
     cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
     const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> lgB;
     const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
-    const cpx<R>* tws = tw_global<R, N>() ? twg + N : tws_s;
+    const cpx<R>* tws = tw_global<R, N>() ? twg + N + tw_key_offset<R, N, K>() : tws_s;
     if constexpr (!tw_global<R, N>()) {
-        if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws_s, twg, tid, blockDim.x);
-        if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws_s, twg, tid, blockDim.x);
+        if constexpr (MODE != INV) fill_stage_twiddles<R, N, false, K>(tws_s, twg, tid, blockDim.x);
+        if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true, K>(tws_s, twg, tid, blockDim.x);
     }
     const int c = cb * B + b;
     const bool cv = c < a.ncol;
@@ -142,13 +149,13 @@ SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smr
     if constexpr (MODE == INV) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = first_element<R, N, true>(t, j);
+            const int e = first_element<K, N, true>(t, j);
             v[j] = cv ? in[e * a.in_es] : czero<R>();
         }
     } else {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = first_element<R, N, false>(t, j);
+            const int e = first_element<K, N, false>(t, j);
             v[j] = (cv && (j % R0) < R0 / 2) ? in[e * a.in_es] : czero<R>();
         }
     }
@@ -166,7 +173,7 @@ SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smr
         const long long mrow = (long long)ko * (a.nh_line + 1);
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const int e = last_element<R, N, false>(t, j);
+            const int e = last_element<K, N, false>(t, j);
             const int ke = e <= N / 2 ? e : N - e;
             mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
         }
@@ -174,39 +181,39 @@ SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smr
     __syncthreads();
     cpx<R>* fresh;
     if constexpr (MODE == INV) {
-        fresh = run_stages<R, N, true, +1, false>(v, sm0, sm1, lay, tws, t);
+        fresh = run_stages<R, N, true, +1, false, K>(v, sm0, sm1, lay, tws, t);
     } else {
-        fresh = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
+        fresh = run_stages<R, N, false, -1, true, K>(v, sm0, sm1, lay, tws, t);
     }
     if constexpr (MODE == XMUL) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             if constexpr (!PREFETCH_M) {
-                const int e = last_element<R, N, false>(t, j);
+                const int e = last_element<K, N, false>(t, j);
                 const int ke = e <= N / 2 ? e : N - e;
                 mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
             }
             v[j] = scale(v[j], mv[j]);
         }
-        run_stages<R, N, true, +1, false>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
+        run_stages<R, N, true, +1, false, K>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
     }
     if constexpr (MODE == FWD) {
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if (cv) out[last_element<R, N, false>(t, j) * a.out_es] = norm(v[j]);
+            if (cv) out[last_element<K, N, false>(t, j) * a.out_es] = norm(v[j]);
     } else {  // the last inverse radix is R0: outputs q < R0/2 are the kept half
 #pragma unroll
         for (int j = 0; j < E; ++j)
-            if ((j % R0) < R0 / 2 && cv) out[last_element<R, N, true>(t, j) * a.out_es] = norm(v[j]);
+            if ((j % R0) < R0 / 2 && cv) out[last_element<K, N, true>(t, j) * a.out_es] = norm(v[j]);
     }
 }
 
-template <class R, int N, int MODE, int LGB>
-__global__ void __launch_bounds__(line_threads<R, N, LGB>(), LGB >= 0 ? min_blocks<R, N, line_threads<R, N, LGB>()>() : 1)
+template <class R, int N, int MODE, int LGB, class K = R>
+__global__ void __launch_bounds__(line_threads<R, N, LGB, K>(), LGB >= 0 ? min_blocks<K, N, line_threads<R, N, LGB, K>()>() : 1)
     k2_line(LArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    line_tile<R, N, MODE, LGB>(a, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
+    line_tile<R, N, MODE, LGB, K>(a, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
 }
 
 // ------------------------------------------------------------------ pipelined line passes
@@ -236,53 +243,53 @@ template <class R, int N, int MODE> constexpr int stage_rows() { return MODE == 
 // The y passes of the 32-value plan at 512 (one exchange a transform) trade the second
 // buffer for a third resident CTA (measured: y passes 10 % faster; the x pass, with two
 // transforms a tile, and the 1024 passes are faster with two buffers and two CTAs).
-template <class R, int N, int MODE> constexpr bool pipe_third_cta()
+template <class R, int N, int MODE, class K = R> constexpr bool pipe_third_cta()
 {
-    return PlanOf<R, N>::E >= 32 && MODE != XMUL && N <= 512;
+    return PlanOf<K, N>::E >= 32 && MODE != XMUL && N <= 512;
 }
-template <class R, int N, int MODE> constexpr bool pipe_two_buffers()
+template <class R, int N, int MODE, class K = R> constexpr bool pipe_two_buffers()
 {
     constexpr int B = 1 << lg_default<N>();
     constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
-    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
-    return !pipe_third_cta<R, N, MODE>() &&
+    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<K, N>();
+    return !pipe_third_cta<R, N, MODE, K>() &&
            twb + 2 * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B <= 110 * 1024;
 }
-template <class R, int N, int MODE> constexpr size_t pipe_smem()
+template <class R, int N, int MODE, class K = R> constexpr size_t pipe_smem()
 {
     constexpr int B = 1 << lg_default<N>();
     constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
-    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<R, N>();
-    return twb + (pipe_two_buffers<R, N, MODE>() ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
+    constexpr size_t twb = sizeof(cpx<R>) * tw_entries<K, N>();
+    return twb + (pipe_two_buffers<R, N, MODE, K>() ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
 }
 
-template <class R, int N, int MODE>
-__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(),
-                                  pipe_third_cta<R, N, MODE>() ? 3 : min_blocks<R, N, line_threads<R, N, lg_default<N>()>()>())
+template <class R, int N, int MODE, class K = R>
+__global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
+                                  pipe_third_cta<R, N, MODE, K>() ? 3 : min_blocks<K, N, line_threads<R, N, lg_default<N>(), K>()>())
     k3_line(PArgs pa)
 {
-    constexpr int E = PlanOf<R, N>::E, T = N / E;
-    constexpr int R0 = PlanOf<R, N>::R[0];
+    constexpr int E = PlanOf<K, N>::E, T = N / E;
+    constexpr int R0 = PlanOf<K, N>::R[0];
     constexpr int LGB = lg_default<N>(), B = 1 << LGB;
     constexpr int NIN = stage_rows<R, N, MODE>();
     constexpr int CH = B * (int)sizeof(cpx<R>) / 16;  // 16-byte chunks per row
     using Lay = LayStrided<R>;
     // cp.async writes 16-byte chunks: the stage must start on a 16-byte boundary
-    static_assert((sizeof(cpx<R>) * tw_entries<R, N>()) % 16 == 0, "twiddle area alignment");
+    static_assert((sizeof(cpx<R>) * tw_entries<K, N>()) % 16 == 0, "twiddle area alignment");
     static_assert((sizeof(cpx<R>) * Lay::size(N, B)) % 16 == 0, "exchange buffer alignment");
     static_assert((B * sizeof(cpx<R>)) % 16 == 0, "stage row alignment");
     const LArgs& a = pa.a;
     const int BUF = Lay::size(N, B);
-    constexpr bool DB = pipe_two_buffers<R, N, MODE>();
+    constexpr bool DB = pipe_two_buffers<R, N, MODE, K>();
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* tws = reinterpret_cast<cpx<R>*>(smraw);
-    cpx<R>* sm0 = tws + tw_entries<R, N>();
+    cpx<R>* sm0 = tws + tw_entries<K, N>();
     cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
     cpx<R>* stg = sm0 + (DB ? 2 : 1) * BUF;
     const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> LGB;
     const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
-    if constexpr (MODE != INV) fill_stage_twiddles<R, N, false>(tws, twg, tid, blockDim.x);
-    if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true>(tws, twg, tid, blockDim.x);
+    if constexpr (MODE != INV) fill_stage_twiddles<R, N, false, K>(tws, twg, tid, blockDim.x);
+    if constexpr (MODE != FWD) fill_stage_twiddles<R, N, true, K>(tws, twg, tid, blockDim.x);
     const Lay lay(LGB, b);
     // tile index = (batch * outer + o) * ncb + cb.  The first tile is decoded by division;
     // each later one adds gridDim.x in that mixed radix (two compares, no division).
@@ -326,11 +333,11 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(),
         cpx<R> v[E];
         if constexpr (MODE == INV) {
 #pragma unroll
-            for (int j = 0; j < E; ++j) v[j] = stg[first_element<R, N, true>(t, j) * B + b];
+            for (int j = 0; j < E; ++j) v[j] = stg[first_element<K, N, true>(t, j) * B + b];
         } else {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                v[j] = ((j % R0) < R0 / 2) ? stg[first_element<R, N, false>(t, j) * B + b] : czero<R>();
+                v[j] = ((j % R0) < R0 / 2) ? stg[first_element<K, N, false>(t, j) * B + b] : czero<R>();
         }
         constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
         R mv[MODE == XMUL ? E : 1];
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(),
         if constexpr (PREFETCH_M) {
 #pragma unroll
             for (int j = 0; j < E; ++j) {
-                const int e = last_element<R, N, false>(t, j);
+                const int e = last_element<K, N, false>(t, j);
                 const int ke = e <= N / 2 ? e : N - e;
                 mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
             }
@@ -349,31 +356,31 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>()>(),
         if (tile + (int)gridDim.x < pa.ntiles) issue(nxt);
         cpx<R>* fresh;
         if constexpr (MODE == INV) {
-            fresh = run_stages<R, N, true, +1, false>(v, sm0, sm1, lay, tws, t);
+            fresh = run_stages<R, N, true, +1, false, K>(v, sm0, sm1, lay, tws, t);
         } else {
-            fresh = run_stages<R, N, false, -1, true>(v, sm0, sm1, lay, tws, t);
+            fresh = run_stages<R, N, false, -1, true, K>(v, sm0, sm1, lay, tws, t);
         }
         if constexpr (MODE == XMUL) {
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 if constexpr (!PREFETCH_M) {
-                    const int e = last_element<R, N, false>(t, j);
+                    const int e = last_element<K, N, false>(t, j);
                     const int ke = e <= N / 2 ? e : N - e;
                     mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
                 }
                 v[j] = scale(v[j], mv[j]);
             }
-            run_stages<R, N, true, +1, false>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
+            run_stages<R, N, true, +1, false, K>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
         }
         cpx<R>* out = static_cast<cpx<R>*>(a.out) + batch * a.out_bs + o * a.out_os + c;
         if constexpr (MODE == FWD) {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                if (cv) out[last_element<R, N, false>(t, j) * a.out_es] = norm(v[j]);
+                if (cv) out[last_element<K, N, false>(t, j) * a.out_es] = norm(v[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                if ((j % R0) < R0 / 2 && cv) out[last_element<R, N, true>(t, j) * a.out_es] = norm(v[j]);
+                if ((j % R0) < R0 / 2 && cv) out[last_element<K, N, true>(t, j) * a.out_es] = norm(v[j]);
         }
         __syncthreads();  // exchange buffers free before the next tile's first write
         cur = nxt;
@@ -532,10 +539,10 @@ template <auto KERNEL> inline sp_status smem_attr(size_t bytes)
     return rc;
 }
 
-template <class R, int N, int MODE>
+template <class R, int N, int MODE, class K = R>
 sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
 {
-    constexpr int E = PlanOf<R, N>::E;
+    constexpr int E = PlanOf<K, N>::E;
     LArgs ab = a;
     ab.B = a.B ? a.B : lanes_b_default<N>();
     const int B = ab.B;
@@ -543,21 +550,21 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     ab.lgB = 0;
     while ((1 << ab.lgB) < B) ++ab.lgB;
     const size_t buf = sizeof(cpx<R>) * LayStrided<R>::size(N, B);
-    const size_t twb = pass_tw_bytes<R, N>();
+    const size_t twb = pass_tw_bytes<R, N, K>();
     const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf;
     dim3 grid((unsigned)((a.ncol + B - 1) / B), (unsigned)outer, (unsigned)batch);
     sp_status rc;
-    constexpr size_t psmem = pipe_smem<R, N, MODE>();
+    constexpr size_t psmem = pipe_smem<R, N, MODE, K>();
     // pipelined persistent kernel: default tile, inputs whose rows are 16-byte aligned
     // (the workspace), and a stage that still leaves two CTAs per SM
     const bool rows_aligned = ((uintptr_t)a.in % 16 == 0) && (a.in_es * sizeof(cpx<R>)) % 16 == 0 &&
                               (a.in_os * sizeof(cpx<R>)) % 16 == 0 && (a.in_bs * sizeof(cpx<R>)) % 16 == 0;
     if (ab.lgB == lg_default<N>() && psmem <= 110 * 1024 && rows_aligned && (a.ncol + B - 1) / B * B <= a.in_ld) {
-        if ((rc = smem_attr<k3_line<R, N, MODE>>(psmem))) return rc;
+        if ((rc = smem_attr<k3_line<R, N, MODE, K>>(psmem))) return rc;
         static std::atomic<int> per_sm_cached{0};  // resident CTAs per SM (same on every GB300)
         int per_sm = per_sm_cached.load(std::memory_order_relaxed);
         if (!per_sm) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_line<R, N, MODE>, (N / E) * B, psmem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_line<R, N, MODE, K>, (N / E) * B, psmem);
             if (per_sm < 1) per_sm = 1;
             per_sm_cached.store(per_sm, std::memory_order_relaxed);
         }
@@ -570,13 +577,13 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
         pa.ncb = (a.ncol + B - 1) / B;
         pa.ntiles = batch * outer * pa.ncb;
         const int nblocks = pa.ntiles < per_sm * sms ? pa.ntiles : per_sm * sms;
-        k3_line<R, N, MODE><<<nblocks, (N / E) * B, psmem, st>>>(pa);
+        k3_line<R, N, MODE, K><<<nblocks, (N / E) * B, psmem, st>>>(pa);
     } else if (ab.lgB == lg_default<N>()) {
-        if ((rc = smem_attr<k2_line<R, N, MODE, lg_default<N>()>>(smem))) return rc;
-        k2_line<R, N, MODE, lg_default<N>()><<<grid, (N / E) * B, smem, st>>>(ab);
+        if ((rc = smem_attr<k2_line<R, N, MODE, lg_default<N>(), K>>(smem))) return rc;
+        k2_line<R, N, MODE, lg_default<N>(), K><<<grid, (N / E) * B, smem, st>>>(ab);
     } else {
-        if ((rc = smem_attr<k2_line<R, N, MODE, -1>>(smem))) return rc;
-        k2_line<R, N, MODE, -1><<<grid, (N / E) * B, smem, st>>>(ab);
+        if ((rc = smem_attr<k2_line<R, N, MODE, -1, K>>(smem))) return rc;
+        k2_line<R, N, MODE, -1, K><<<grid, (N / E) * B, smem, st>>>(ab);
     }
     return sp_cuda_check(cudaGetLastError(), "v2 line pass");
 }
@@ -614,16 +621,16 @@ __global__ void k_stage_twiddles(cpx<R>* dst, const cpx<R>* __restrict__ tw)
 
 template <class F> inline sp_status with_len(int N, F&& f);
 
-// K: the plan key of the passes that read the table (R for the line passes, ZKey<R> for
-// the z passes).
+// K: the plan key of the passes that read the table (R and, where it exists, the
+// alternative LineKey<R, 1> for the line passes; ZKey<R> for the z passes).
 template <class R, class K> struct StageTw {
     cpx<R>* tw;
     cudaStream_t st;
     template <int N> sp_status run()
     {
-        if constexpr (tw_global<R, N>()) {
-            static_assert(tw_stage_size<K, N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
-            k_stage_twiddles<R, N, K><<<16, 256, 0, st>>>(tw + N, tw);
+        if constexpr (tw_global<R, N>() && (KeyVariant<K>::v == 0 || AltPlan<R, N>::exists)) {
+            static_assert(tw_key_offset<R, N, K>() + tw_stage_size<K, N>() <= SP_TW_STAGED_MAX, "staged twiddle room");
+            k_stage_twiddles<R, N, K><<<16, 256, 0, st>>>(tw + N + tw_key_offset<R, N, K>(), tw);
             return sp_cuda_check(cudaGetLastError(), "staged twiddles");
         }
         return SP_OK;
@@ -649,12 +656,55 @@ inline bool len_ok(int N)
     return N == 64 || N == 128 || N == 192 || N == 256 || N == 384 || N == 512 || N == 1024;
 }
 
+// variant 1: the alternative radix plan of this type and length (AltPlan), where it exists
 template <class R, int MODE> struct LineRun {
     const LArgs* a;
     int outer, batch;
     cudaStream_t st;
-    template <int N> sp_status run() { return launch_line<R, N, MODE>(*a, outer, batch, st); }
+    int variant;
+    template <int N> sp_status run()
+    {
+        if constexpr (AltPlan<R, N>::exists) {
+            if (variant) return launch_line<R, N, MODE, LineKey<R, 1>>(*a, outer, batch, st);
+        } else {
+            if (variant) return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no alternative radix plan for length %d", N);
+        }
+        return launch_line<R, N, MODE>(*a, outer, batch, st);
+    }
 };
+
+// Radices of the plans a solve uses: out[8 ax + s] for stage s of axis ax's passes (the
+// x pass, the y passes, the z passes), 0 after the last stage.
+template <class K, int N> void copy_radices(int* out)
+{
+    for (int s = 0; s < 8; ++s) out[s] = s < PlanOf<K, N>::NS ? PlanOf<K, N>::R[s] : 0;
+}
+template <class R> struct RadicesOf {
+    int* out;
+    int variant;  // -1: the z passes' plan
+    template <int N> sp_status run()
+    {
+        if (variant < 0) {
+            copy_radices<ZKey<R>, N>(out);
+        } else {
+            if constexpr (AltPlan<R, N>::exists) {
+                if (variant) {
+                    copy_radices<LineKey<R, 1>, N>(out);
+                    return SP_OK;
+                }
+            }
+            copy_radices<R, N>(out);
+        }
+        return SP_OK;
+    }
+};
+template <class R> sp_status radices(sp_plan p, int* out)
+{
+    sp_status rc;
+    for (int ax = 0; ax < 2; ++ax)
+        if ((rc = with_len(p->N[ax], RadicesOf<R>{out + 8 * ax, p->line_variant[ax]}))) return rc;
+    return with_len(p->N[2], RadicesOf<R>{out + 16, -1});
+}
 
 template <class R, class Tio> struct ZRun {
     const ZArgs2* a;
@@ -678,6 +728,7 @@ template <class R> sp_status stage_twiddles(sp_plan p, cudaStream_t st)
         cpx<R>* tw = static_cast<cpx<R>*>(const_cast<void*>(Tabs<R>::tw(p, ax)));
         sp_status rc = ax == 2 ? with_len(p->N[ax], StageTw<R, ZKey<R>>{tw, st}) : with_len(p->N[ax], StageTw<R, R>{tw, st});
         if (rc) return rc;
+        if (ax < 2 && (rc = with_len(p->N[ax], StageTw<R, LineKey<R, 1>>{tw, st}))) return rc;
     }
     return SP_OK;
 }
@@ -729,11 +780,11 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     if (mark && (rc = sp_mark(p, st))) return rc;
     if ((rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, batch, st}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st}))) return rc;
+    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st, p->line_variant[1]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st}))) return rc;
+    if ((rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st, p->line_variant[0]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st}))) return rc;
+    if ((rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st, p->line_variant[1]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
     if ((rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, batch, st}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
@@ -747,7 +798,7 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
 // own workspace slices, as in the solve).  Host-synchronising.  Returns the mean
 // milliseconds per launch, or a negative value on error.
 template <class R, class Tio>
-float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
+float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, int variant)
 {
     ZArgs2 z = {};
     z.rho = p->d_work;
@@ -789,10 +840,10 @@ float time_pass(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_
             rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, batch, st});
             if (rc == SP_OK) rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, batch, st});
         } else if (pass == 1) {
-            rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st});
-            if (rc == SP_OK) rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st});
+            rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st, variant});
+            if (rc == SP_OK) rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st, variant});
         } else {
-            rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st});
+            rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st, variant});
         }
     }
     cudaEventRecord(e1, st);
@@ -1071,8 +1122,8 @@ sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
     x.tw = Tabs<R>::tw(p, 0);
     sp_status rc;
     if ((rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, 1, st}))) return rc;
-    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], 1, st}))) return rc;
-    return with_len(p->N[0], LineRun<R, FWD>{&x, p->N[1], 1, st});
+    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], 1, st, p->line_variant[1]}))) return rc;
+    return with_len(p->N[0], LineRun<R, FWD>{&x, p->N[1], 1, st, p->line_variant[0]});
 }
 
 }  // namespace v2
@@ -1083,6 +1134,14 @@ sp_status forward(sp_plan p, const void* rho, void* spec, cudaStream_t st)
     PREFIX template sp_status v2::launch_line<R, N, v2::FWD>(const v2::LArgs&, int, int, cudaStream_t); \
     PREFIX template sp_status v2::launch_line<R, N, v2::INV>(const v2::LArgs&, int, int, cudaStream_t); \
     PREFIX template sp_status v2::launch_line<R, N, v2::XMUL>(const v2::LArgs&, int, int, cudaStream_t);
+// The line-pass launchers of the alternative radix plan (AltPlan) of type R at length N.
+#define SP_V2_ALT(PREFIX, R, N)                                                                   \
+    PREFIX template sp_status v2::launch_line<R, N, v2::FWD, LineKey<R, 1>>(const v2::LArgs&, int, int,  \
+                                                                             cudaStream_t);      \
+    PREFIX template sp_status v2::launch_line<R, N, v2::INV, LineKey<R, 1>>(const v2::LArgs&, int, int,  \
+                                                                             cudaStream_t);      \
+    PREFIX template sp_status v2::launch_line<R, N, v2::XMUL, LineKey<R, 1>>(const v2::LArgs&, int, int, \
+                                                                              cudaStream_t);
 #define SP_V2_LINES(PREFIX, R)        \
     SP_V2_LINES_N(PREFIX, R, 64)      \
     SP_V2_LINES_N(PREFIX, R, 128)     \

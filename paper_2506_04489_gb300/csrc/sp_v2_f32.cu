@@ -2,6 +2,9 @@
 #include "sp_v2.cuh"
 
 SP_V2_LINES(extern, float)
+SP_V2_ALT(extern, float, 256)
+SP_V2_ALT(extern, float, 512)
+SP_V2_ALT(extern, float, 1024)
 
 namespace v2 {
 template <> const void* Tabs<float>::tw(sp_plan p, int ax) { return p->d_tw32[ax]; }
@@ -19,10 +22,13 @@ sp_status sp_v2_forward_f32(sp_plan p, const void* rho, void* spec, cudaStream_t
     return mixed ? v2::forward<float, double>(p, rho, spec, st) : v2::forward<float, float>(p, rho, spec, st);
 }
 
-float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed)
+float sp_v2_time_pass_f32(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, bool mixed, int variant)
 {
-    return mixed ? v2::time_pass<float, double>(p, pass, tile, batch, iters, st) : v2::time_pass<float, float>(p, pass, tile, batch, iters, st);
+    return mixed ? v2::time_pass<float, double>(p, pass, tile, batch, iters, st, variant)
+                 : v2::time_pass<float, float>(p, pass, tile, batch, iters, st, variant);
 }
+
+sp_status sp_v2_radices_f32(sp_plan p, int* out) { return v2::radices<float>(p, out); }
 
 sp_status sp_v2_stage_twiddles_f32(sp_plan p, cudaStream_t st)
 {
@@ -34,3 +40,11 @@ sp_status sp_v2_persistent_f32(sp_plan p, const void* rho, void* u, int batch, c
     return mixed ? v2::solve_persistent<float, double>(p, rho, u, batch, st)
                  : v2::solve_persistent<float, float>(p, rho, u, batch, st);
 }
+
+namespace {
+struct HasAltF32 {
+    template <int N> sp_status run() { return AltPlan<float, N>::exists ? SP_OK : SP_ERR_UNSUPPORTED_SIZE; }
+};
+}  // namespace
+
+bool sp_v2_has_alt_f32(int N) { return v2::with_len(N, HasAltF32{}) == SP_OK; }

@@ -18,10 +18,12 @@ sp_status sp_v2_forward_f64(sp_plan p, const void* rho, void* spec, cudaStream_t
     return v2::forward<double, double>(p, rho, spec, st);
 }
 
-float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st)
+float sp_v2_time_pass_f64(sp_plan p, int pass, int tile, int batch, int iters, cudaStream_t st, int variant)
 {
-    return v2::time_pass<double, double>(p, pass, tile, batch, iters, st);
+    return v2::time_pass<double, double>(p, pass, tile, batch, iters, st, variant);
 }
+
+sp_status sp_v2_radices_f64(sp_plan p, int* out) { return v2::radices<double>(p, out); }
 
 sp_status sp_v2_persistent_f64(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st)
 {

@@ -182,9 +182,29 @@ class Plan:
 
     # ----------------------------------------------------------------- batched execution
     def autotune(self, batch: int = 1, stream=None) -> dict:
-        """Pick the pass tiles for `batch` right-hand sides by timing (results unchanged)."""
+        """Pick the pass tiles and the line passes' radix plans for `batch` right-hand
+        sides by timing; returns launch_config()."""
         self._N.check(self._N.lib.sp_plan_autotune(self._h, int(batch), _stream_handle(stream)), "sp_plan_autotune")
-        return self.tiles()
+        return self.launch_config()
+
+    def launch_config(self) -> dict:
+        """Tiles, radix-plan choice per axis and the radices of the passes in use."""
+        line = (ctypes.c_int * 3)()
+        z = ctypes.c_int()
+        plan = (ctypes.c_int * 3)()
+        rad = (ctypes.c_int * 24)()
+        self._N.check(self._N.lib.sp_plan_launch_config(self._h, line, ctypes.byref(z), plan, rad),
+                      "sp_plan_launch_config")
+        radices = {ax: tuple(r for r in rad[8 * i:8 * i + 8] if r) for i, ax in enumerate(("x", "y", "z"))}
+        return {"line": tuple(line), "z": z.value, "line_plan": tuple(plan), "radices": radices}
+
+    def set_launch_config(self, line=None, z: int = None, line_plan=None) -> None:
+        """Set tiles and line radix plans (sp_plan_set_launch_config); None keeps a part."""
+        cur = self.launch_config()
+        lt = (ctypes.c_int * 3)(*(line if line is not None else cur["line"]))
+        lp = (ctypes.c_int * 3)(*(line_plan if line_plan is not None else cur["line_plan"]))
+        self._N.check(self._N.lib.sp_plan_set_launch_config(self._h, lt, int(cur["z"] if z is None else z), lp),
+                      "sp_plan_set_launch_config")
 
     def tiles(self) -> dict:
         line = (ctypes.c_int * 3)()

@@ -26,12 +26,16 @@ def rhs():
 def test_batched_graph_matches_alone_and_oracle(oracle, rhs, precision):
     plan = Plan(N, LO, HI, precision=precision, max_batch=BATCH)
     rho = rhs.to("cuda", dtype=plan.dtype)
-    # reference: every right-hand side alone, with the default tiles
-    alone = torch.stack([plan.solve(rho[b].contiguous()) for b in range(BATCH)])
     tiles = plan.autotune(BATCH)
     assert tiles["z"] > 0 and tiles["line"][0] > 0 and tiles["line"][1] > 0
+    # reference: every right-hand side alone, in the same launch configuration (the tuner
+    # may have picked another radix plan, which rounds differently)
+    alone = torch.stack([plan.solve(rho[b].contiguous()) for b in range(BATCH)])
     out = torch.empty_like(rho)
     stream = torch.cuda.Stream()
+    # the plan's solves share one workspace: the capture's solves on `stream` must follow
+    # the ones above on the current stream
+    stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
         graph = plan.capture(rho, out, stream)
         out.zero_()

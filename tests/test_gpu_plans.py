@@ -56,10 +56,54 @@ def test_radix_plan_matches_oracle(oracle, n, precision):
     scale = np.abs(ref).max()
     u_default = plan.solve(t).double().cpu().numpy()
     assert np.abs(u_default - ref).max() / scale <= TOL[precision], "built-in tiles"
-    tiles = plan.autotune(1)
+    cfg = plan.autotune(1)
     u_tuned = plan.solve(t).double().cpu().numpy()
-    assert np.abs(u_tuned - ref).max() / scale <= TOL[precision], ("autotuned tiles", tiles)
-    # tiles regroup lines into CTAs and never change a line's arithmetic
-    assert np.array_equal(u_default, u_tuned), tiles
+    assert np.abs(u_tuned - ref).max() / scale <= TOL[precision], ("autotuned", cfg)
+    if cfg["line_plan"] == (0, 0, 0):
+        # tiles regroup lines into CTAs and never change a line's arithmetic
+        assert np.array_equal(u_default, u_tuned), cfg
     plan.sync()
+    plan.close()
+
+
+# FP32 and mixed at 2n = 256, 512, 1024 and double-float at 256 have an alternative radix
+# plan for the line passes (x pass, y passes), which the autotuner may choose.
+ALT = {"fp32": (256, 512, 1024), "mixed": (256, 512, 1024), "df32": (256,)}
+
+
+def _alt_cases():
+    out = []
+    for precision, lengths in ALT.items():
+        for N in lengths:
+            for axis in (0, 1):
+                n = [32, 32, 32]
+                n[axis] = N // 2
+                out.append((precision, tuple(n), axis))
+    return out
+
+
+@pytest.mark.parametrize("precision,n,axis", _alt_cases())
+def test_alternative_radix_plan_matches_oracle(oracle, precision, n, axis):
+    rho, ref = _reference(oracle, n)
+    plan = Plan(n, LO, HI, precision=precision)
+    line_plan = [0, 0, 0]
+    line_plan[axis] = 1
+    for tile in (0, 2):  # built-in tile (the pipelined kernel where it fits) and a runtime tile
+        line = [0, 0, 0]
+        line[axis] = tile
+        plan.set_launch_config(line=line, line_plan=line_plan)
+        cfg = plan.launch_config()
+        assert cfg["line_plan"][axis] == 1
+        u = plan.solve(torch.from_numpy(rho).to("cuda", dtype=plan.dtype)).double().cpu().numpy()
+        assert np.abs(u - ref).max() / np.abs(ref).max() <= TOL[precision], cfg
+    plan.sync()
+    plan.close()
+
+
+def test_launch_config_rejects_absent_plans():
+    from paper_2506_04489_gb300._native import SuperpotError
+    plan = Plan((64, 32, 32), LO, HI, precision="fp64")  # no alternative plans in native FP64
+    with pytest.raises(SuperpotError) as e:
+        plan.set_launch_config(line_plan=(1, 0, 0))
+    assert e.value.status == "SP_ERR_UNSUPPORTED_SIZE"
     plan.close()
