@@ -261,6 +261,8 @@ int sp_plan_pass_times(sp_plan plan, double* total_ms, int* launches, const char
  *   eight- or sixteen-value plans beside the built-in 16-16, 32-16, 32-32; double-float
  *   at 256: 16-16 beside 8-8-4), the line passes of each axis also time it; another plan
  *   rounds differently, so results then agree to the precision's tolerance, not bitwise.
+ *   FP32 and mixed plans where the fused plane passes exist then time whole solves of
+ *   both schedules and keep the faster (see sp_plan_launch_config).
  *   A no-op for grids without compiled register-resident passes.
  * sp_plan_tiles -- the tiles in use: line_tiles[3] (columns per CTA of the y and x line
  *   passes, by axis; 0 = default) and *z_tile (pairs of real lines per CTA of the z
@@ -276,21 +278,29 @@ sp_status sp_plan_tiles(const sp_plan plan, int* line_tiles, int* z_tile);
  *                            1: the y passes; 0 built-in, 1 the alternative plan);
  *   radices[24]            : radices[8 ax + s] = radix of stage s of the forward transform
  *                            of the passes along axis ax (x pass, y passes, z passes), 0
- *                            after the last stage.
+ *                            after the last stage (the five-pass schedule's plans);
+ *   *schedule              : 0 five passes, 1 the three-pass schedule with fused plane
+ *                            passes (FP32 and mixed at 2n1 = 2n2 = 512: the z and y
+ *                            transforms of an x-plane in one launch of 8-CTA clusters,
+ *                            exchanging through distributed shared memory; its y phase uses
+ *                            the eight-value plan), 2 the persistent single launch.
  * Any pointer may be NULL.
  */
-sp_status sp_plan_launch_config(const sp_plan plan, int* line_tiles, int* z_tile, int* line_plan, int* radices);
+sp_status sp_plan_launch_config(const sp_plan plan, int* line_tiles, int* z_tile, int* line_plan, int* radices,
+                                int* schedule);
 
 /*
  * sp_plan_set_launch_config -- set a launch configuration instead of tuning one (for
  * example one that sp_plan_autotune chose earlier and the caller saved): line_tiles[3]
  * and z_tile as sp_plan_tiles reports them (0 = built-in), line_plan[3] as
- * sp_plan_launch_config reports it (index 2 must be 0).  A NULL pointer leaves that part
- * unchanged.  A radix plan that does not exist for the type and length is
- * SP_ERR_UNSUPPORTED_SIZE; a tile outside a pass's range fails at the next solve with
- * SP_ERR_INVALID.
+ * sp_plan_launch_config reports it (index 2 must be 0), schedule 0 (five passes) or 1
+ * (fused plane passes; -1 leaves it unchanged; the persistent launch is set with
+ * sp_plan_set_persistent).  A NULL pointer leaves that part unchanged.  A radix plan or a
+ * schedule that does not exist for the type and grid is SP_ERR_UNSUPPORTED_SIZE; a tile
+ * outside a pass's range fails at the next solve with SP_ERR_INVALID.
  */
-sp_status sp_plan_set_launch_config(sp_plan plan, const int* line_tiles, int z_tile, const int* line_plan);
+sp_status sp_plan_set_launch_config(sp_plan plan, const int* line_tiles, int z_tile, const int* line_plan,
+                                    int schedule);
 
 /*
  * CUDA-graph capture of a (batched) solve on fixed buffers, replayed with one launch.

@@ -76,9 +76,9 @@ lib.sp_plan_set_kernel.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_autotune.restype = ctypes.c_int
 lib.sp_plan_autotune.argtypes = [_vp, ctypes.c_int, _vp]
 lib.sp_plan_launch_config.restype = ctypes.c_int
-lib.sp_plan_launch_config.argtypes = [_vp, _ip, _ip, _ip, _ip]
+lib.sp_plan_launch_config.argtypes = [_vp, _ip, _ip, _ip, _ip, _ip]
 lib.sp_plan_set_launch_config.restype = ctypes.c_int
-lib.sp_plan_set_launch_config.argtypes = [_vp, _ip, ctypes.c_int, _ip]
+lib.sp_plan_set_launch_config.argtypes = [_vp, _ip, ctypes.c_int, _ip, ctypes.c_int]
 lib.sp_plan_tiles.restype = ctypes.c_int
 lib.sp_plan_tiles.argtypes = [_vp, _ip, _ip]
 lib.sp_graph_capture.restype = ctypes.c_int

@@ -63,13 +63,25 @@ extern "C" sp_status sp_plan_autotune(sp_plan p, int batch, sp_stream stream)
     p->tile_line[0] = best_tile[2];
     p->line_variant[1] = best_variant[1];
     p->line_variant[0] = best_variant[2];
+    // FP32 and mixed: the fused three-pass schedule against the five passes, whole solves
+    p->plane_fused = false;
+    if ((p->prec == SP_FP32 || p->prec == SP_MIXED) && sp_v2_plane_supported_f32(p)) {
+        const bool mixed = p->prec == SP_MIXED;
+        const float five = sp_v2_time_solve_f32(p, batch, 5, st, mixed);
+        p->plane_fused = true;
+        const float fused = sp_v2_time_solve_f32(p, batch, 5, st, mixed);
+        sp_clear_error();
+        p->plane_fused = fused > 0.f && (five < 0.f || fused < five);
+    }
     return sp_cuda_check(cudaStreamSynchronize(st), "autotune");
 }
 
-extern "C" sp_status sp_plan_launch_config(const sp_plan p, int* line_tiles, int* z_tile, int* line_plan, int* radices)
+extern "C" sp_status sp_plan_launch_config(const sp_plan p, int* line_tiles, int* z_tile, int* line_plan, int* radices,
+                                           int* schedule)
 {
     sp_clear_error();
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
+    if (schedule) *schedule = p->persistent ? 2 : (p->plane_fused ? 1 : 0);
     if (line_tiles)
         for (int ax = 0; ax < 3; ++ax) line_tiles[ax] = p->tile_line[ax];
     if (z_tile) *z_tile = p->tile_z;
@@ -96,11 +108,15 @@ extern "C" sp_status sp_plan_launch_config(const sp_plan p, int* line_tiles, int
     return SP_OK;
 }
 
-extern "C" sp_status sp_plan_set_launch_config(sp_plan p, const int* line_tiles, int z_tile, const int* line_plan)
+extern "C" sp_status sp_plan_set_launch_config(sp_plan p, const int* line_tiles, int z_tile, const int* line_plan,
+                                               int schedule)
 {
     sp_clear_error();
     if (!p) return sp_fail(SP_ERR_INVALID, "plan is NULL");
     if (z_tile < 0) return sp_fail(SP_ERR_INVALID, "z_tile must be >= 0 (got %d)", z_tile);
+    if (schedule < -1 || schedule > 1) return sp_fail(SP_ERR_INVALID, "schedule must be -1, 0 or 1 (got %d)", schedule);
+    if (schedule == 1 && !((p->prec == SP_FP32 || p->prec == SP_MIXED) && sp_v2_plane_supported_f32(p)))
+        return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "no fused plane passes for this grid and precision");
     if (line_tiles)
         for (int ax = 0; ax < 3; ++ax)
             if (line_tiles[ax] < 0) return sp_fail(SP_ERR_INVALID, "line_tiles[%d] must be >= 0", ax);
@@ -124,6 +140,7 @@ extern "C" sp_status sp_plan_set_launch_config(sp_plan p, const int* line_tiles,
     p->tile_z = z_tile;
     if (line_plan)
         for (int ax = 0; ax < 2; ++ax) p->line_variant[ax] = line_plan[ax];
+    if (schedule >= 0) p->plane_fused = schedule == 1;
     return SP_OK;
 }
 

@@ -79,6 +79,9 @@ struct sp_plan_s {
     // radix plan of the line passes per axis (0: built-in, 1: the alternative plan of the
     // type and length), chosen by the autotuner
     int line_variant[3];
+    // FP32 and mixed: the three-pass schedule with fused plane passes (z and y transforms
+    // of an x-plane in one cluster launch), where it exists; chosen by the autotuner
+    bool plane_fused;
     // solves run as one persistent cooperative launch (sp_plan_set_persistent)
     bool persistent;
     // pass timing (diagnostic): events recorded between passes while timing is on.  The
@@ -137,6 +140,8 @@ float sp_v2_time_pass_df(sp_plan p, int pass, int tile, int batch, int iters, cu
 // radices of the register-resident passes in use: out[8 ax + s], ax = x, y, z passes
 // whether the type has an alternative radix plan for the line passes at padded length N
 bool sp_v2_has_alt_f32(int N);
+bool sp_v2_plane_supported_f32(sp_plan p);
+float sp_v2_time_solve_f32(sp_plan p, int batch, int iters, cudaStream_t st, bool mixed);
 bool sp_v2_has_alt_df(int N);
 sp_status sp_v2_radices_f32(sp_plan p, int* out);
 sp_status sp_v2_radices_f64(sp_plan p, int* out);

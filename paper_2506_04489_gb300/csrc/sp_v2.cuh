@@ -118,6 +118,26 @@ template <class R, int N, int LGB, class K = R> constexpr int line_threads()
 }
 template <int N> constexpr int lg_default() { return N >= 1024 ? 2 : 3; }
 
+// ------------------------------------------------------------------ asynchronous copies
+SP_D void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+SP_D void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+SP_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+SP_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The x pass of the 8-byte-multiplier types (double-float, FP64) copies each thread's
+// multiplier values into shared memory with cp.async when its tile starts, so the loads
+// overlap the forward transform without holding registers; N B values of R per CTA.
+template <class R, int MODE> constexpr bool stage_m() { return MODE == XMUL && sizeof(R) >= 8; }
+template <class R, int N, int MODE> constexpr size_t stage_m_bytes(int B) { return stage_m<R, MODE>() ? sizeof(R) * (size_t)N * B : 0; }
+
 // One tile of a line pass: B columns (c = cb B + b) of outer index o, right-hand side
 // `batch`; all threads of the block take part.  `smraw` is the pass's dynamic shared
 // memory (staged twiddles where they live in shared memory, then the exchange buffers).
@@ -159,24 +179,33 @@ SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smr
             v[j] = (cv && (j % R0) < R0 / 2) ? in[e * a.in_es] : czero<R>();
         }
     }
-    // x pass, FP32: the multiplier values of this thread's outputs are loaded before the
-    // forward transform, so their latency overlaps its arithmetic (the wider types keep
-    // the registers for the transform and load them after it)
+    // x pass: the multiplier values of this thread's outputs are fetched before the forward
+    // transform, so their latency overlaps its arithmetic: into registers for FP32, into
+    // shared memory by cp.async for the 8-byte types (whose registers hold the transform)
     constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
+    constexpr bool STAGE_M = stage_m<R, MODE>();
     R mv[MODE == XMUL ? E : 1];
     const R* M = static_cast<const R*>(a.M);
     const int ko = o <= a.No / 2 ? o : a.No - o;
     const long long mrow = (long long)ko * (a.nh_line + 1);
+    R* mst = reinterpret_cast<R*>(sm1 + BUF);  // STAGE_M: [j][thread]
     if constexpr (PREFETCH_M) {
-        const R* M = static_cast<const R*>(a.M);
-        const int ko = o <= a.No / 2 ? o : a.No - o;
-        const long long mrow = (long long)ko * (a.nh_line + 1);
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const int e = last_element<K, N, false>(t, j);
             const int ke = e <= N / 2 ? e : N - e;
             mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
         }
+    } else if constexpr (STAGE_M) {
+        if (cv) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int e = last_element<K, N, false>(t, j);
+                const int ke = e <= N / 2 ? e : N - e;
+                cp_async8(&mst[j * blockDim.x + tid], &M[(mrow + ke) * a.ldzM + c]);
+            }
+        }
+        cp_async_commit();
     }
     __syncthreads();
     cpx<R>* fresh;
@@ -186,9 +215,12 @@ SP_D void line_tile(const LArgs& a, int cb, int o, int batch, unsigned char* smr
         fresh = run_stages<R, N, false, -1, true, K>(v, sm0, sm1, lay, tws, t);
     }
     if constexpr (MODE == XMUL) {
+        if constexpr (STAGE_M) cp_async_wait_all();  // this thread's own copies: no barrier needed
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            if constexpr (!PREFETCH_M) {
+            if constexpr (STAGE_M) {
+                mv[j] = cv ? mst[j * blockDim.x + tid] : Num<R>::c(0.0);
+            } else if constexpr (!PREFETCH_M) {
                 const int e = last_element<K, N, false>(t, j);
                 const int ke = e <= N / 2 ? e : N - e;
                 mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
@@ -222,13 +254,6 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB, K>(), LGB >= 0 ? min_b
 // complex values each) are copied into a shared-memory stage with cp.async; after the
 // threads have moved the current tile's values from the stage into registers, the copies
 // of the next tile are issued, so they land while the current tile computes.
-SP_D void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-SP_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-SP_D void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 struct PArgs {
     LArgs a;
@@ -551,7 +576,7 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     while ((1 << ab.lgB) < B) ++ab.lgB;
     const size_t buf = sizeof(cpx<R>) * LayStrided<R>::size(N, B);
     const size_t twb = pass_tw_bytes<R, N, K>();
-    const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf;
+    const size_t smem = twb + (two_buffers(buf, twb) ? 2 : 1) * buf + stage_m_bytes<R, N, MODE>(B);
     dim3 grid((unsigned)((a.ncol + B - 1) / B), (unsigned)outer, (unsigned)batch);
     sp_status rc;
     constexpr size_t psmem = pipe_smem<R, N, MODE, K>();
@@ -935,7 +960,7 @@ template <class R, int N> constexpr size_t persist_smem()
     constexpr int B = 1 << persist_lgb<R, N>();
     constexpr size_t lbuf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
     constexpr size_t ltw = pass_tw_bytes<R, N>();
-    constexpr size_t line = ltw + (two_buffers(lbuf, ltw) ? 2 : 1) * lbuf;
+    constexpr size_t line = ltw + (two_buffers(lbuf, ltw) ? 2 : 1) * lbuf + stage_m_bytes<R, N, XMUL>(B);
     constexpr size_t zbuf = sizeof(cpx<R>) * (size_t)persist_bz<R, N>() * LayLine<N>::LD;
     constexpr size_t ztw = pass_tw_bytes<R, N, ZKey<R>>();
     constexpr size_t zs = ztw + (two_buffers(zbuf, ztw) ? 2 : 1) * zbuf;

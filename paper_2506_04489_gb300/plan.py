@@ -193,17 +193,21 @@ class Plan:
         z = ctypes.c_int()
         plan = (ctypes.c_int * 3)()
         rad = (ctypes.c_int * 24)()
-        self._N.check(self._N.lib.sp_plan_launch_config(self._h, line, ctypes.byref(z), plan, rad),
+        sched = ctypes.c_int()
+        self._N.check(self._N.lib.sp_plan_launch_config(self._h, line, ctypes.byref(z), plan, rad, ctypes.byref(sched)),
                       "sp_plan_launch_config")
         radices = {ax: tuple(r for r in rad[8 * i:8 * i + 8] if r) for i, ax in enumerate(("x", "y", "z"))}
-        return {"line": tuple(line), "z": z.value, "line_plan": tuple(plan), "radices": radices}
+        schedule = {0: "five_passes", 1: "fused_planes", 2: "persistent"}[sched.value]
+        return {"line": tuple(line), "z": z.value, "line_plan": tuple(plan), "radices": radices, "schedule": schedule}
 
-    def set_launch_config(self, line=None, z: int = None, line_plan=None) -> None:
-        """Set tiles and line radix plans (sp_plan_set_launch_config); None keeps a part."""
+    def set_launch_config(self, line=None, z: int = None, line_plan=None, schedule: str = None) -> None:
+        """Set tiles, line radix plans and the schedule ("five_passes" or "fused_planes")
+        (sp_plan_set_launch_config); None keeps a part."""
         cur = self.launch_config()
         lt = (ctypes.c_int * 3)(*(line if line is not None else cur["line"]))
         lp = (ctypes.c_int * 3)(*(line_plan if line_plan is not None else cur["line_plan"]))
-        self._N.check(self._N.lib.sp_plan_set_launch_config(self._h, lt, int(cur["z"] if z is None else z), lp),
+        sc = {None: -1, "five_passes": 0, "fused_planes": 1}[schedule]
+        self._N.check(self._N.lib.sp_plan_set_launch_config(self._h, lt, int(cur["z"] if z is None else z), lp, sc),
                       "sp_plan_set_launch_config")
 
     def tiles(self) -> dict:

@@ -77,6 +77,14 @@ def test_256_against_oracle(oracle, dens, precision, record_property):
           f"{e_tuned:.3e} (autotuned {tiles})")
     assert e_default <= TOL[precision]
     assert e_tuned <= TOL[precision]
+    if precision in ("fp32", "mixed"):  # both schedules, whichever the tuner kept
+        plan = Plan(n, LO, HI, precision=precision)
+        for schedule in ("fused_planes", "five_passes"):
+            plan.set_launch_config(schedule=schedule)
+            e = _rel(_solve(plan, rho), ref)
+            print(f"256^3 {dens} {precision} {schedule}: max-norm rel err vs oracle {e:.3e}")
+            assert e <= TOL[precision], schedule
+        plan.close()
 
 
 @pytest.mark.parametrize("precision", ["df32", "fp64", "fp32", "mixed"])
