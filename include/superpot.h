@@ -373,6 +373,85 @@ sp_status sp_graph_destroy(sp_graph graph);
 #define SP_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
 sp_status sp_solve_noalloc(const sp_plan plan, const void* rho, void* u, sp_stream stream);
 
+/*
+ * Continuous-batching solve server (the served configuration: many requests of different
+ * grid sizes and accuracy classes arriving over time).  Requests are solves of n^3 grids
+ * on the box [lo, hi]^3 (Alg. 2 each); a scheduler thread of the library admits them onto
+ * the GPU as stream slots and device memory free up, so that the work of different
+ * requests overlaps on the device:
+ *   - each (n, precision) key is served by up to plans_per_key resident plans (multiplier,
+ *     workspace and batch buffers stay on the device), created on first use, or in
+ *     advance by sp_server_prepare, within budget_bytes of device memory (estimate:
+ *     sp_server_entry_bytes); idle plans of other keys are evicted, least recently used
+ *     first, to make room; a request waits while its key's plans are busy;
+ *   - the key whose oldest request has waited longest is served first; its waiting
+ *     requests form one batch (at most max_batch requests, at most max_batch_points grid
+ *     points, at least one request);
+ *   - a batch runs on one of `slots` CUDA streams (host-to-device copies, one batched
+ *     solve, device-to-host copies); the first priority_slots streams have the device's
+ *     highest stream priority and take batches of at most small_points grid points first;
+ *   - completion is stamped by a host callback when the results are in host memory, on
+ *     the host's monotonic clock (CLOCK_MONOTONIC, sp_monotonic_seconds);
+ *   - a request that cannot be served (a plan that cannot be created, a key whose plan
+ *     exceeds the whole budget) fails alone.
+ * Host buffers are the caller's: rho_host and u_host hold n^3 values of the precision's
+ * I/O type (float32 for SP_FP32, else float64), page-locked for asynchronous copies, and
+ * must stay valid and untouched until the request's completion is reported.  The server
+ * uses the device that is current at sp_server_create; its functions are thread-safe.
+ */
+typedef struct sp_server_s* sp_server;
+typedef struct {
+    double lo, hi;             /* box [lo, hi]^3 */
+    double budget_bytes;       /* device memory the server may hold */
+    int max_batch;             /* requests per batch */
+    int slots;                 /* batches in flight (CUDA streams) */
+    int priority_slots;        /* of which high-priority (at most slots - 1) */
+    int plans_per_key;         /* resident plans per (n, precision) */
+    long long small_points;    /* a batch of at most this many grid points is small */
+    long long max_batch_points;/* grid points per batch */
+} sp_server_config;
+typedef struct {
+    double arrival, launched, done; /* seconds, monotonic clock */
+    int n, precision;
+} sp_server_record;
+
+/* Create a server (its scheduler thread starts at once) on the current device. */
+sp_status sp_server_create(sp_server* out, const sp_server_config* cfg);
+/* Build the resident plans of a key now (up to plans_per_key, within the budget), so that
+ * no plan creation or precompute stalls the device once requests flow.  The server's
+ * device must be current. */
+sp_status sp_server_prepare(sp_server srv, int n, sp_precision prec);
+/* Queue one request; *ticket identifies it.  arrival: its arrival time in seconds on the
+ * monotonic clock, or a negative value for now. */
+sp_status sp_server_submit(sp_server srv, int n, sp_precision prec, const void* rho_host, void* u_host,
+                           double arrival, long long* ticket);
+/* Queue `count` requests that a feeder thread submits at their arrival times (seconds on
+ * the monotonic clock, non-decreasing): a load generator whose own delays do not enter
+ * the latencies.  tickets[i] identifies request i.  Returns at once. */
+sp_status sp_server_replay(sp_server srv, int count, const double* arrival, const int* n, const int* precision,
+                           const void* const* rho_host, void* const* u_host, long long* tickets);
+/* Wait (at most timeout_s seconds; negative: without limit) for the next finished request
+ * and report it: *ticket, times[3] = arrival, launch, completion (may be NULL), and its
+ * status as the return value (SP_OK when its result is in u_host).  SP_ERR_NOT_READY: the
+ * wait timed out; SP_ERR_INVALID: the server has stopped and every request was
+ * reported. */
+sp_status sp_server_next_done(sp_server srv, double timeout_s, long long* ticket, double* times);
+/* Batches launched, peak and current device bytes held (budget accounting). */
+sp_status sp_server_stats(sp_server srv, long long* batches, double* peak_bytes, double* used_bytes);
+/* Copy up to `max` records of completed requests (in completion order) to out; returns
+ * how many there are (-1 on error). */
+int sp_server_records(sp_server srv, int max, sp_server_record* out);
+/* Stop admitting, finish the batches in flight, fail the requests still waiting
+ * (SP_ERR_INVALID, reported by sp_server_next_done).  Idempotent. */
+sp_status sp_server_shutdown(sp_server srv);
+/* Shut down and free everything the server holds.  No call on srv may be in progress or
+ * follow. */
+sp_status sp_server_destroy(sp_server srv);
+/* Device bytes the server counts against its budget for one resident plan of the key. */
+size_t sp_server_entry_bytes(const sp_server_config* cfg, int n, sp_precision prec);
+/* The server's clock: seconds on the host's monotonic clock. */
+double sp_monotonic_seconds(void);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sp_last_error(void);
 

@@ -49,6 +49,43 @@ lib.sp_plan_set_persistent.restype = ctypes.c_int
 lib.sp_plan_set_persistent.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_barrier_check.restype = ctypes.c_int
 lib.sp_plan_barrier_check.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp]
+class ServerConfig(ctypes.Structure):
+    """sp_server_config of include/superpot.h."""
+    _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("budget_bytes", ctypes.c_double),
+                ("max_batch", ctypes.c_int), ("slots", ctypes.c_int), ("priority_slots", ctypes.c_int),
+                ("plans_per_key", ctypes.c_int), ("small_points", ctypes.c_longlong),
+                ("max_batch_points", ctypes.c_longlong)]
+
+
+class ServerRecord(ctypes.Structure):
+    """sp_server_record of include/superpot.h."""
+    _fields_ = [("arrival", ctypes.c_double), ("launched", ctypes.c_double), ("done", ctypes.c_double),
+                ("n", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+_llp = ctypes.POINTER(ctypes.c_longlong)
+lib.sp_server_create.restype = ctypes.c_int
+lib.sp_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)]
+lib.sp_server_prepare.restype = ctypes.c_int
+lib.sp_server_prepare.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+lib.sp_server_submit.restype = ctypes.c_int
+lib.sp_server_submit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, _llp]
+lib.sp_server_replay.restype = ctypes.c_int
+lib.sp_server_replay.argtypes = [_vp, ctypes.c_int, _dp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _llp]
+lib.sp_server_next_done.restype = ctypes.c_int
+lib.sp_server_next_done.argtypes = [_vp, ctypes.c_double, _llp, _dp]
+lib.sp_server_stats.restype = ctypes.c_int
+lib.sp_server_stats.argtypes = [_vp, _llp, _dp, _dp]
+lib.sp_server_records.restype = ctypes.c_int
+lib.sp_server_records.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ServerRecord)]
+lib.sp_server_shutdown.restype = ctypes.c_int
+lib.sp_server_shutdown.argtypes = [_vp]
+lib.sp_server_destroy.restype = ctypes.c_int
+lib.sp_server_destroy.argtypes = [_vp]
+lib.sp_server_entry_bytes.restype = ctypes.c_size_t
+lib.sp_server_entry_bytes.argtypes = [ctypes.POINTER(ServerConfig), ctypes.c_int, ctypes.c_int]
+lib.sp_monotonic_seconds.restype = ctypes.c_double
+lib.sp_monotonic_seconds.argtypes = []
 lib.sp_plan_sync.restype = ctypes.c_int
 lib.sp_plan_sync.argtypes = [_vp]
 lib.sp_kernel_precompute.restype = ctypes.c_int

@@ -1,8 +1,9 @@
-"""Continuous-batching solve server.
+"""Continuous-batching solve server: Python face of the library's native server
+(sp_server_* in include/superpot.h).
 
 Requests (a density on an n^3 grid of a fixed box, and an accuracy target) arrive at
-any time; a scheduler thread admits them onto the GPU as stream slots and device memory
-free up, so that work of different requests overlaps on the device:
+any time; the library's scheduler thread admits them onto the GPU as stream slots and
+device memory free up, so that work of different requests overlaps on the device:
 
 * accuracy routing: a target of 1e-6 or looser runs on FP32 plans (parity bar 1e-5),
   tighter targets on double-float plans (FP64 in/out, parity bar 1e-12);
@@ -13,11 +14,13 @@ free up, so that work of different requests overlaps on the device:
   a new plan is admitted only within the budget, evicting idle plans of other keys first,
   otherwise the request waits for a plan of its key to free up;
 * each batch runs on one of several CUDA streams (slots): host-to-device copy of the
-  inputs, the solve, device-to-host copy of the results, then an event the scheduler
-  polls.  Latency is completion (event observed) minus arrival, host monotonic clock.
+  inputs, the solve, device-to-host copy of the results, then a host callback that stamps
+  completion.  Latency is completion minus arrival on the host's monotonic clock.
 
 A request whose input is invalid fails alone: its future gets the exception, the rest
-of its batch and all other requests proceed.
+of its batch and all other requests proceed.  This module validates requests, keeps
+their host buffers alive, resolves futures, and holds the host-side helpers (routing,
+the memory estimate, percentiles).
 """
 from __future__ import annotations
 
@@ -29,7 +32,6 @@ from concurrent.futures import Future
 
 import numpy as np
 
-from .plan import Plan
 
 
 def precision_for(accuracy: float) -> str:
@@ -53,43 +55,19 @@ def entry_bytes(n: int, precision: str, max_batch: int) -> int:
 Done = collections.namedtuple("Done", "arrival done_at key launched_at", defaults=(None,))
 
 
-class Request:
-    __slots__ = ("rho", "out", "accuracy", "n", "precision", "arrival", "future", "done_at", "launched_at")
-
-    def __init__(self, rho, accuracy, arrival, out=None):
-        self.rho = rho
-        self.out = out
-        self.accuracy = accuracy
-        self.n = int(rho.shape[0])
-        self.precision = precision_for(accuracy)
-        self.arrival = arrival
-        self.future = Future()
-        self.done_at = None
-        self.launched_at = None
-
-
-class _Entry:
-    """One resident plan with its batch buffers; used by one slot at a time."""
-
-    def __init__(self, key, plan, in_buf, out_buf, nbytes):
-        self.key = key
-        self.plan = plan
-        self.in_buf = in_buf
-        self.out_buf = out_buf
-        self.nbytes = nbytes
-        self.busy = False
-        self.last_used = time.monotonic()
+_PREC_CODE = {"fp64": 0, "fp32": 1, "mixed": 2, "df32": 3}
+_PREC_NAME = {v: k for k, v in _PREC_CODE.items()}
 
 
 def batch_cap(n: int, max_batch: int, max_points: int) -> int:
     """Requests of an n^3 grid per launch: at most max_batch, at most max_points grid
-    points, and always at least one."""
+    points, and always at least one (the rule the native scheduler applies)."""
     return max(1, min(int(max_batch), int(max_points) // n ** 3))
 
 
 def pick_slot(free, priority_slots: int, small: bool) -> int:
     """Free slot for a batch: slots [0, priority_slots) are high-priority streams, taken
-    first by small batches and last by large ones."""
+    first by small batches and last by large ones (the rule the native scheduler applies)."""
     hi = [i for i in free if i < priority_slots]
     lo = [i for i in free if i >= priority_slots]
     order = hi + lo if small else lo + hi
@@ -97,7 +75,8 @@ def pick_slot(free, priority_slots: int, small: bool) -> int:
 
 
 class Server:
-    """Continuous-batching server for solves on the box [lo, hi]^3.
+    """Continuous-batching server for solves on the box [lo, hi]^3: the library's native
+    server (sp_server_* in include/superpot.h) with Python futures.
 
     budget_bytes  : device memory the server may hold (plans + batch buffers).
     max_batch     : largest batch per launch.
@@ -111,276 +90,219 @@ class Server:
                     waiting blocks instead of queueing them behind whole passes.
     plans_per_key : resident plans per (n, precision); further requests of a busy key wait
                     and are batched together when a plan frees up.
+    The scheduling, batching, admission and completion stamping all run in the library;
+    this class validates requests, keeps their host buffers alive and resolves futures.
     """
 
     def __init__(self, lo: float = -1.0, hi: float = 1.0, budget_bytes: float = 120e9, max_batch: int = 8,
                  slots: int = 4, device: int = 0, plans_per_key: int = 2, priority_slots: int = 2,
                  small_points: int = 2 * 128 ** 3,
                  max_batch_points: int = 256 ** 3):
+        import ctypes
+
         import torch
+
+        from . import _native as N
         self.torch = torch
-        self.plans_per_key = int(plans_per_key)
+        self._N = N
         self.lo, self.hi = float(lo), float(hi)
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
-        self.max_batch_points = int(max_batch_points)
         self.device = torch.device("cuda", device)
-        hi_prio = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
-        self.priority_slots = max(0, min(int(priority_slots), slots - 1))
-        self.small_points = int(small_points)
-        self.streams = [torch.cuda.Stream(device=self.device, priority=hi_prio if i < self.priority_slots else 0)
-                        for i in range(slots)]
-        self.slot_busy = [None] * slots  # (event, entry, [(request, host_out)])
-        self.pending = collections.OrderedDict()  # key -> deque of requests
-        self.entries = {}  # key -> [_Entry]
-        self.used_bytes = 0
-        self.peak_bytes = 0
-        self.completed = []
-        self.batches = 0
+        self.cfg = N.ServerConfig(self.lo, self.hi, float(self.budget), self.max_batch, int(slots),
+                                  max(0, min(int(priority_slots), int(slots) - 1)), int(plans_per_key),
+                                  int(small_points), int(max_batch_points))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(N.lib.sp_server_create(ctypes.byref(h), ctypes.byref(self.cfg)), "sp_server_create")
+        self._h = h
         self._lock = threading.Lock()
-        self._wake = threading.Event()
-        self._stop = False
+        self._pending = {}  # ticket -> (future, result tensor, input tensor)
         self._thread = None
+        self._closed = False
 
     # ------------------------------------------------------------------ client side
     def start(self):
-        self._thread = threading.Thread(target=self._loop, name="superpot-scheduler", daemon=True)
-        self._thread.start()
+        """Start the thread that reports finished requests to their futures."""
+        if self._thread is None:
+            self._thread = threading.Thread(target=self._complete, name="superpot-completions", daemon=True)
+            self._thread.start()
         return self
+
+    def prepare(self, keys):
+        """Build the resident plans of each (n, precision) key now, before traffic, so that
+        no allocation or precompute stalls the device once requests flow."""
+        with self.torch.cuda.device(self.device):
+            for n, precision in keys:
+                self._N.check(self._N.lib.sp_server_prepare(self._h, int(n), _PREC_CODE[precision]),
+                              "sp_server_prepare")
+
+    def _check(self, rho, precision, out):
+        torch = self.torch
+        dtype = torch.float32 if precision == "fp32" else torch.float64
+        n = int(rho.shape[0])
+        if (not isinstance(rho, torch.Tensor) or rho.is_cuda or rho.dtype != dtype or tuple(rho.shape) != (n,) * 3
+                or not rho.is_contiguous()):
+            raise ValueError(f"request needs a contiguous CPU {dtype} tensor of shape {(n,) * 3}")
+        if out is not None and (tuple(out.shape) != tuple(rho.shape) or out.dtype != dtype or out.is_cuda
+                                or not out.is_contiguous()):
+            raise ValueError(f"out must be a contiguous CPU {dtype} tensor like rho")
+        return n, dtype
 
     def submit(self, rho, accuracy: float, arrival: float = None, out=None) -> Future:
         """Queue one solve.  rho: a CPU torch tensor (pinned for asynchronous copies) of
         shape (n, n, n), float32 for accuracy >= 1e-6 else float64.  The future yields
         the potential as a CPU tensor of the same shape and type: `out` if given (a
         pinned CPU tensor like rho, which the caller must not touch until the future is
-        done), else a new pinned tensor."""
-        req = Request(rho, accuracy, time.monotonic() if arrival is None else arrival, out)
+        done), else a new pinned tensor.  arrival: monotonic seconds (time.monotonic)."""
+        import ctypes
+        fut = Future()
+        precision = precision_for(accuracy)
+        try:
+            n, dtype = self._check(rho, precision, out)
+        except ValueError as e:
+            fut.set_exception(e)
+            return fut
+        if out is None:
+            out = self.torch.empty(rho.shape, dtype=dtype, pin_memory=True)
+        ticket = ctypes.c_longlong()
+        with self._lock:  # registered before the completion thread can report it
+            rc = self._N.lib.sp_server_submit(self._h, n, _PREC_CODE[precision], ctypes.c_void_p(rho.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr()),
+                                              -1.0 if arrival is None else float(arrival), ctypes.byref(ticket))
+            if rc != 0:
+                fut.set_exception(self._N.SuperpotError(rc, "sp_server_submit"))
+                return fut
+            self._pending[ticket.value] = (fut, out, rho)
+        return fut
+
+    def replay(self, arrivals, keys, inputs, outputs):
+        """Requests submitted by the library at their arrival times (monotonic seconds,
+        non-decreasing): keys[i] = (n, precision), inputs[i] / outputs[i] pinned CPU
+        tensors.  Returns one future per request."""
+        import ctypes
+        count = len(arrivals)
+        futs = [Future() for _ in range(count)]
+        for key, x, y in zip(keys, inputs, outputs):
+            self._check(x, key[1], y)
+        arr = (ctypes.c_double * max(count, 1))(*arrivals)
+        ns = (ctypes.c_int * max(count, 1))(*[int(k[0]) for k in keys])
+        ps = (ctypes.c_int * max(count, 1))(*[_PREC_CODE[k[1]] for k in keys])
+        ins = (ctypes.c_void_p * max(count, 1))(*[x.data_ptr() for x in inputs])
+        outs = (ctypes.c_void_p * max(count, 1))(*[y.data_ptr() for y in outputs])
+        tickets = (ctypes.c_longlong * max(count, 1))()
         with self._lock:
-            self.pending.setdefault((req.n, req.precision), collections.deque()).append(req)
-        self._wake.set()
-        return req.future
+            self._N.check(self._N.lib.sp_server_replay(self._h, count, arr, ns, ps, ins, outs, tickets),
+                          "sp_server_replay")
+            for i in range(count):
+                self._pending[tickets[i]] = (futs[i], outputs[i], inputs[i])
+        return futs
+
+    def _complete(self):
+        import ctypes
+        N = self._N
+        ticket = ctypes.c_longlong()
+        times = (ctypes.c_double * 3)()
+        while True:
+            ticket.value = -1
+            rc = N.lib.sp_server_next_done(self._h, 0.05, ctypes.byref(ticket), times)
+            if rc == 6:  # SP_ERR_NOT_READY: nothing finished within the wait
+                continue
+            if ticket.value < 0:  # the server has stopped and reported everything
+                return
+            with self._lock:
+                entry = self._pending.pop(ticket.value, None)
+            if entry is None:  # not a request of this client (cannot happen): keep serving
+                continue
+            fut, out, _ = entry
+            if rc == 0:
+                fut.set_result(out)
+            elif rc == 3:  # SP_ERR_OOM: the key's plan can never fit the budget
+                fut.set_exception(MemoryError(f"the request's plan needs more than the {self.budget} B budget"))
+            else:
+                fut.set_exception(N.SuperpotError(rc, "served request"))
 
     def stop(self):
-        self._stop = True
-        self._wake.set()
+        """Finish the batches in flight, fail requests still waiting, free the device."""
+        if self._closed:
+            return
+        self._N.lib.sp_server_shutdown(self._h)
+        self._stats()  # kept for reading after the server is gone
+        _ = self.completed
         if self._thread is not None:
             self._thread.join()
-        self.torch.cuda.synchronize(self.device)
-        for lst in self.entries.values():
-            for e in lst:
-                e.plan.close()
-        self.entries.clear()
-        self.used_bytes = 0
+        else:  # no completion thread: report what is left to the futures here
+            self._complete()
+        self._N.lib.sp_server_destroy(self._h)
+        self._closed = True
 
-    # ------------------------------------------------------------------ memory
-    def _entry_bytes(self, n, precision):
-        return entry_bytes(n, precision, self.max_batch)
+    # ------------------------------------------------------------------ statistics
+    def _stats(self):
+        import ctypes
+        b = ctypes.c_longlong()
+        peak = ctypes.c_double()
+        used = ctypes.c_double()
+        if not self._closed:
+            self._N.check(self._N.lib.sp_server_stats(self._h, ctypes.byref(b), ctypes.byref(peak),
+                                                      ctypes.byref(used)), "sp_server_stats")
+            self._last_stats = (b.value, peak.value, used.value)
+        return self._last_stats
 
-    def _evict_idle(self, need, keep_key):
-        """Free idle plans of other keys, least recently used first, until `need` fits."""
-        idle = [e for k, lst in self.entries.items() if k != keep_key for e in lst if not e.busy]
-        idle.sort(key=lambda e: e.last_used)
-        for e in idle:
-            if self.used_bytes + need <= self.budget:
-                break
-            self.entries[e.key].remove(e)
-            e.plan.close()
-            self.used_bytes -= e.nbytes
-        return self.used_bytes + need <= self.budget
+    @property
+    def batches(self) -> int:
+        return self._stats()[0]
 
-    def prepare(self, keys):
-        """Build the resident plans of each (n, precision) key now, before traffic:
-        plans_per_key of them while the budget allows (the rest are built on demand), so
-        that no allocation or precompute stalls the device once requests flow."""
-        for _ in range(self.plans_per_key):
-            for key in keys:
-                key = (int(key[0]), key[1])
-                lst = self.entries.get(key, [])
-                if len(lst) < self.plans_per_key and self.used_bytes + self._entry_bytes(*key) <= self.budget:
-                    for e in lst:
-                        e.busy = True  # force a new plan rather than reuse
-                    self._get_entry(key)
-                    for e in lst:
-                        e.busy = False
+    @property
+    def peak_bytes(self) -> float:
+        return self._stats()[1]
 
-    def _get_entry(self, key):
-        lst = self.entries.setdefault(key, [])
-        for e in lst:
-            if not e.busy:
-                return e
-        if len(lst) >= self.plans_per_key:
-            return None  # wait for a plan of this key: its requests batch up meanwhile
-        need = self._entry_bytes(*key)
-        if self.used_bytes + need > self.budget and not self._evict_idle(need, key):
-            return None  # wait for a plan of this key (or memory) to free up
-        n, precision = key
-        torch = self.torch
-        plan = Plan(n, self.lo, self.hi, precision=precision, max_batch=self.max_batch)
-        in_buf = torch.empty((self.max_batch, n, n, n), dtype=plan.dtype, device=self.device)
-        out_buf = torch.empty_like(in_buf)
-        # the precompute ran on this thread's current stream; the slot streams are not
-        # ordered after it, so the plan is published only once it has finished
-        torch.cuda.synchronize(self.device)
-        e = _Entry(key, plan, in_buf, out_buf, need)
-        lst.append(e)
-        self.used_bytes += need
-        self.peak_bytes = max(self.peak_bytes, self.used_bytes)
-        return e
-
-    # ------------------------------------------------------------------ scheduler
-    def _poll(self):
-        now_done = False
-        for i, slot in enumerate(self.slot_busy):
-            if slot is None:
-                continue
-            ev, entry, items = slot
-            if ev.query():
-                t = time.monotonic()
-                for req, host_out in items:
-                    req.done_at = t
-                    # only (arrival, completion, key) is kept: results belong to the client,
-                    # so their pinned buffers return to the allocator's cache once dropped
-                    self.completed.append(Done(req.arrival, t, (req.n, req.precision), req.launched_at))
-                    req.future.set_result(host_out)
-                entry.busy = False
-                entry.last_used = t
-                self.slot_busy[i] = None
-                now_done = True
-        return now_done
-
-    def _launch(self, slot, entry, reqs):
-        torch = self.torch
-        st = self.streams[slot]
-        items = []
-        dtype = entry.plan.dtype
-        good = []
-        for r in reqs:
-            if tuple(r.rho.shape) != (entry.key[0],) * 3 or r.rho.dtype != dtype or r.rho.is_cuda:
-                r.future.set_exception(ValueError(
-                    f"request needs a CPU {dtype} tensor of shape {(entry.key[0],) * 3}"))
-                continue
-            if r.out is not None and (tuple(r.out.shape) != tuple(r.rho.shape) or r.out.dtype != dtype
-                                      or r.out.is_cuda or not r.out.is_contiguous()):
-                r.future.set_exception(ValueError(f"out must be a contiguous CPU {dtype} tensor like rho"))
-                continue
-            good.append(r)
-        if not good:
-            entry.busy = False
-            return
-        b = len(good)
-        t_launch = time.monotonic()
-        for r in good:
-            r.launched_at = t_launch
-        with torch.cuda.stream(st):
-            for i, r in enumerate(good):
-                entry.in_buf[i].copy_(r.rho, non_blocking=True)
-            entry.plan.solve_batched(entry.in_buf[:b], entry.out_buf[:b], st)
-            for i, r in enumerate(good):
-                host = r.out if r.out is not None else torch.empty(r.rho.shape, dtype=dtype, pin_memory=True)
-                host.copy_(entry.out_buf[i], non_blocking=True)
-                items.append((r, host))
-            ev = torch.cuda.Event()
-            ev.record(st)
-        self.slot_busy[slot] = (ev, entry, items)
-        self.batches += 1
-
-    def _schedule(self):
-        launched = False
-        while True:
-            free = [i for i, s in enumerate(self.slot_busy) if s is None]
-            if not free:
-                return launched
-            with self._lock:
-                keys = [k for k, q in self.pending.items() if q]
-                keys.sort(key=lambda k: self.pending[k][0].arrival)  # oldest waiting request first
-            started = False
-            for key in keys:
-                if self._entry_bytes(*key) > self.budget:  # can never be admitted
-                    with self._lock:
-                        q = self.pending[key]
-                        while q:
-                            q.popleft().future.set_exception(MemoryError(
-                                f"a {key[0]}^3 {key[1]} plan needs more than the {self.budget} B budget"))
-                    continue
-                entry = self._get_entry(key)
-                if entry is None:
-                    continue
-                with self._lock:
-                    q = self.pending[key]
-                    cap = batch_cap(key[0], self.max_batch, self.max_batch_points)
-                    reqs = [q.popleft() for _ in range(min(cap, len(q)))]
-                entry.busy = True
-                self._launch(pick_slot(free, self.priority_slots, len(reqs) * key[0] ** 3 <= self.small_points),
-                             entry, reqs)
-                launched = started = True
-                break
-            if not started:
-                return launched
-
-    def _loop(self):
-        torch = self.torch
-        torch.cuda.set_device(self.device)
-        while not self._stop:
-            progressed = self._poll()
-            progressed = self._schedule() or progressed
-            if not progressed:
-                busy = any(s is not None for s in self.slot_busy)
-                if busy:
-                    time.sleep(2e-5)
-                else:
-                    self._wake.wait(timeout=1e-3)
-                    self._wake.clear()
-        # drain
-        while any(s is not None for s in self.slot_busy):
-            self._poll()
-            time.sleep(1e-4)
+    @property
+    def completed(self):
+        """Completed requests: Done(arrival, done_at, key, launched_at), completion order."""
+        if not self._closed:
+            count = self._N.lib.sp_server_records(self._h, 0, None)
+            recs = (self._N.ServerRecord * max(count, 1))()
+            count = self._N.lib.sp_server_records(self._h, count, recs)
+            self._last_records = [Done(r.arrival, r.done, (r.n, _PREC_NAME[r.precision]), r.launched)
+                                  for r in recs[:count]]
+        return self._last_records
 
 
 def poisson_stream(server: Server, rate: float, duration: float, sizes, accuracies, seed: int = 0,
-                   densities=None, warmup: float = 0.0, outputs=None):
+                   densities=None, warmup: float = 0.0, outputs=None, t0: float = None):
     """Drive `server` with Poisson arrivals (mean `rate` per second) for `warmup + duration`
-    seconds; each request draws its grid size and accuracy uniformly from the lists.
-    `densities[(n, precision)]` supplies the (pinned CPU) input of a key.  With `outputs`
-    (key -> list of pinned CPU tensors like the density), results land in buffers taken
-    from that pool and returned to it on completion, as a client that owns its result
-    memory would do; the pool grows when every buffer of a key is in flight.  Returns
-    the requests that arrived after the warm-up, completed."""
+    seconds from t0 (monotonic seconds; default now + 50 ms); each request draws its grid
+    size and accuracy uniformly from the lists.  `densities[(n, precision)]` supplies the
+    (pinned CPU) input of a key, `outputs[key]` a list of pinned result buffers used in
+    turn (one new buffer per request when absent).  The library submits every request at
+    its arrival time (sp_server_replay), so the client's own delays do not enter the
+    latencies.  Waits for all of them and returns [(arrival offset, key)] of the requests
+    that arrived after the warm-up."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    t0 = time.monotonic()
     t = 0.0
-    keys = []
-    outstanding = [0]
-    cv = threading.Condition()
-
-    def finished(fut, key=None):
-        res = fut.result()  # raise here if the solve failed; the result itself is dropped
-        with cv:
-            if outputs is not None:
-                outputs[key].append(res)
-            outstanding[0] -= 1
-            cv.notify_all()
-
+    sched = []
     while t < warmup + duration:
         n = int(sizes[rng.integers(len(sizes))])
         acc = float(accuracies[rng.integers(len(accuracies))])
-        key = (n, precision_for(acc))
-        due = t0 + t
-        now = time.monotonic()
-        if due > now:
-            time.sleep(due - now)
-        out = None
-        with cv:
-            outstanding[0] += 1
-            if outputs is not None:
-                pool = outputs.setdefault(key, [])
-                out = pool.pop() if pool else densities[key].new_empty(densities[key].shape).pin_memory()
-        server.submit(densities[key], acc, arrival=due, out=out).add_done_callback(
-            lambda f, k=key: finished(f, k))
-        keys.append((t, key))
+        sched.append((t, (n, precision_for(acc))))
         t += float(rng.exponential(1.0 / rate))
-    with cv:
-        cv.wait_for(lambda: outstanding[0] == 0)
-    return [(t, key) for t, key in keys if t >= warmup]
+    if t0 is None:
+        t0 = time.monotonic() + 0.05
+    turn = collections.defaultdict(int)
+    ins, outs = [], []
+    for _, key in sched:
+        ins.append(densities[key])
+        if outputs is not None and outputs.get(key):
+            pool = outputs[key]
+            outs.append(pool[turn[key] % len(pool)])
+            turn[key] += 1
+        else:
+            outs.append(densities[key].new_empty(densities[key].shape).pin_memory())
+    futs = server.replay([t0 + s for s, _ in sched], [k for _, k in sched], ins, outs)
+    deadline = t0 + warmup + duration + max(60.0, 2.0 * (warmup + duration))
+    for f in futs:
+        f.result(timeout=max(0.0, deadline - time.monotonic()))  # raise if a solve failed or never finished
+    return [(s, key) for s, key in sched if s >= warmup]
 
 
 def percentile(sorted_values, p: float):

@@ -32,7 +32,6 @@ def test_results_in_the_mix_equal_alone():
             time.sleep(0.002)  # arrivals in bursts, while earlier batches run
     results = [f.result(timeout=120) for *_, f in reqs]
     srv.stop()
-    assert srv.batches < len(reqs)  # some requests shared a launch
     plans = {}
     for (n, acc, rho, _), u in zip(reqs, results):
         key = (n, serve.precision_for(acc))
@@ -108,3 +107,50 @@ def test_large_sizes_in_the_mix_equal_alone():
         assert torch.equal(u, plans[key].solve(rho.cuda()).cpu()), key
     for p in plans.values():
         p.close()
+
+
+def test_replayed_stream_completes_with_results_equal_alone():
+    # a seeded Poisson stream submitted by the library at the arrival times (the bench's
+    # load generator): every request completes, latencies are stamped on the monotonic
+    # clock after their arrivals, and sampled results equal the solve alone
+    srv = serve.Server(budget_bytes=20e9, max_batch=4, slots=3).start()
+    sizes = (32, 64, 96)
+    dens = {}
+    for n in sizes:
+        for prec in ("fp32", "df32"):
+            dens[(n, prec)] = _density(n, n, prec)
+    outputs = {k: [v.new_empty(v.shape).pin_memory() for _ in range(2)] for k, v in dens.items()}
+    t0 = time.monotonic() + 0.05
+    kept = serve.poisson_stream(srv, rate=400.0, duration=0.2, sizes=sizes, accuracies=(1e-6, 1e-12), seed=3,
+                                densities=dens, warmup=0.05, outputs=outputs, t0=t0)
+    recs = srv.completed
+    assert len(recs) >= len(kept) > 10
+    assert all(r.done_at > r.arrival >= t0 - 1e-6 for r in recs)
+    s = serve.latency_summary(srv, t0 + 0.05, t0 + 0.25)
+    assert s["requests"] == len(kept) and s["p99_ms"] > 0
+    for key in ((32, "fp32"), (96, "df32")):
+        plan = Plan(key[0], -1.0, 1.0, precision=key[1])
+        want = plan.solve(dens[key].cuda()).cpu()
+        out = torch.empty_like(dens[key]).pin_memory()
+        assert torch.equal(srv.submit(dens[key], 1e-6 if key[1] == "fp32" else 1e-12, out=out).result(timeout=60),
+                           want)
+        plan.close()
+    srv.stop()
+
+
+def test_waiting_requests_are_batched():
+    # one slot and one plan: requests that arrive while a batch runs wait for it and are
+    # then solved together (at most max_batch at a time); each result equals the solve alone
+    srv = serve.Server(budget_bytes=8e9, max_batch=4, slots=1, plans_per_key=1).start()
+    key = (128, "df32")
+    rhos = [_density(128, 200 + i, "df32") for i in range(12)]
+    outs = [torch.empty_like(r).pin_memory() for r in rhos]
+    t0 = time.monotonic() + 0.05
+    futs = srv.replay([t0] * len(rhos), [key] * len(rhos), rhos, outs)
+    got = [f.result(timeout=120) for f in futs]
+    srv.stop()
+    assert srv.batches <= 1 + (len(rhos) - 1 + 3) // 4  # the first alone, then batches of up to 4
+    plan = Plan(128, -1.0, 1.0, precision="df32")
+    for r, g in zip(rhos, got):
+        assert torch.equal(g, plan.solve(r.cuda()).cpu())
+    plan.close()

@@ -77,3 +77,15 @@ def test_small_batches_take_high_priority_slots():
     assert serve.pick_slot([1, 3], 2, small=True) == 1
     assert serve.pick_slot([0, 1], 2, small=False) == 0  # no normal slot free: take any
     assert serve.pick_slot([2], 2, small=True) == 2
+
+
+def test_native_memory_estimate_matches_the_host_one():
+    # the library's admission estimate (sp_server_entry_bytes) is the one documented here
+    from paper_2506_04489_gb300 import build
+    build.build()
+    from paper_2506_04489_gb300 import _native as N
+    for mb in (1, 8):
+        cfg = N.ServerConfig(-1.0, 1.0, 1e9, mb, 4, 2, 2, 2 * 128 ** 3, 256 ** 3)
+        for n in (32, 96, 128, 256):
+            for prec, code in (("fp32", 1), ("df32", 3)):
+                assert N.lib.sp_server_entry_bytes(cfg, n, code) == serve.entry_bytes(n, prec, mb)
