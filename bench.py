@@ -116,8 +116,9 @@ def minimal_bytes_per_point(prec):
 
 # Sources of the solve-pass kernels (the plan, setup, graph and API files do not change
 # what a pass executes); ncu counts are valid while their hash is unchanged.
-PASS_SOURCES = ("sp_common.cuh", "sp_df32.cuh", "sp_fft.cuh", "sp_v2.cuh", "sp_passes.cu", "sp_v2_df.cu",
-                "sp_v2_df_lines.cu", "sp_v2_f32.cu", "sp_v2_f32_lines.cu", "sp_v2_f64.cu", "sp_v2_f64_lines.cu")
+PASS_SOURCES = ("sp_common.cuh", "sp_df32.cuh", "sp_fft.cuh", "sp_v2.cuh", "sp_plane.cuh", "sp_passes.cu",
+                "sp_v2_df.cu", "sp_v2_df_lines.cu", "sp_v2_df_alt.cu", "sp_v2_f32.cu", "sp_v2_f32_lines.cu",
+                "sp_v2_f32_alt.cu", "sp_v2_f64.cu", "sp_v2_f64_lines.cu")
 
 
 def source_hash():
