@@ -90,6 +90,8 @@ struct LArgs {
     const void* tw;                  // exp(-2 pi i j / N), j < N
     const void* M;                   // XMUL: multiplier [|ko|][|kl|][kz], row stride ldzM
     int No, nh_line, ldzM;
+    int reverse;                     // walk the outer index from the end: the previous pass
+                                     // wrote its last outer indices last, so they are still in L2
 };
 
 // Largest column tile of a line pass (the launch bound of the runtime-tile kernel):
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(line_threads<R, N, LGB, K>(), LGB >= 0 ? min_b
     k2_line(LArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    line_tile<R, N, MODE, LGB, K>(a, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
+    line_tile<R, N, MODE, LGB, K>(a, blockIdx.x, a.reverse ? gridDim.y - 1 - blockIdx.y : blockIdx.y, blockIdx.z, smraw);
 }
 
 // ------------------------------------------------------------------ pipelined line passes
@@ -334,8 +336,9 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
         return x;
     };
     auto issue = [&](TileIdx x) {
+        const int xo = a.reverse ? pa.outer - 1 - x.o : x.o;
         const char* src = reinterpret_cast<const char*>(static_cast<const cpx<R>*>(a.in) + x.batch * a.in_bs +
-                                                        x.o * a.in_os + x.cb * B);
+                                                        xo * a.in_os + x.cb * B);
         for (int q = tid; q < NIN * CH; q += blockDim.x) {
             const int row = q / CH, ch = q % CH;
             cp_async16(reinterpret_cast<char*>(stg) + (size_t)row * B * sizeof(cpx<R>) + ch * 16,
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
     if (blockIdx.x < pa.ntiles) issue(cur);
     for (int tile = blockIdx.x; tile < pa.ntiles; tile += gridDim.x) {
         const TileIdx nxt = advance(cur);
-        const int batch = cur.batch, o = cur.o, cb = cur.cb;
+        const int batch = cur.batch, o = a.reverse ? pa.outer - 1 - cur.o : cur.o, cb = cur.cb;
         const int c = cb * B + b;
         const bool cv = c < a.ncol;
         cp_async_wait_all();
@@ -425,6 +428,8 @@ struct ZArgs2 {
     long long io_bs, w_bs;
     const void* tw;
     int B;                // pairs of real lines per CTA (pairs_max<N>() / 2^j)
+    int reverse;          // walk the lines from the end (their planes were written last by the
+                          // previous pass, so they are still in L2)
 };
 
 template <int N> constexpr int pairs_max() { return N >= 512 ? 8 : (N >= 256 ? 16 : 32); }
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
                                   min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_fwd(ZArgs2 a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    zf_tile<R, Tio, N>(a, blockIdx.x, blockIdx.y, smraw);
+    zf_tile<R, Tio, N>(a, a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, blockIdx.y, smraw);
 }
 
 // One tile of the z inverse pass (pairs of real output lines), as zf_tile.
@@ -542,7 +547,7 @@ __global__ void __launch_bounds__((N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>(),
                                   min_blocks<ZKey<R>, N, (N / PlanOf<ZKey<R>, N>::E) * pairs_max<N>()>()) k2_z_inv(ZArgs2 a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    zi_tile<R, Tio, N>(a, blockIdx.x, blockIdx.y, smraw);
+    zi_tile<R, Tio, N>(a, a.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, blockIdx.y, smraw);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -771,7 +776,7 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     p->pass_name[2] = "x_multiply";
     p->pass_name[3] = "y_inverse";
     p->pass_name[4] = "z_inverse";
-    ZArgs2 z;
+    ZArgs2 z = {};
     z.rho = rho;
     z.u = u;
     z.W = p->d_work;
@@ -802,16 +807,24 @@ sp_status solve(sp_plan p, const void* rho, void* u, int batch, cudaStream_t st,
     x.No = p->N[1];
     x.nh_line = p->n[0];
     x.ldzM = p->ldz;
+    // Each pass writes its outer indices in increasing order, so what it wrote last is still
+    // in L2 when the next pass starts: the y forward pass walks the planes the z forward
+    // pass wrote from the last one down, and the z inverse pass the rows the y inverse pass
+    // wrote (the x pass reads every plane in every tile, so its order does not matter).
+    LArgs yf = y, yi = y;
+    yf.reverse = 1;
+    ZArgs2 zf = z, zi = z;
+    zi.reverse = 1;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[2], ZRun<R, Tio>{&z, true, batch, st}))) return rc;
+    if ((rc = with_len(p->N[2], ZRun<R, Tio>{&zf, true, batch, st}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&y, p->n[0], batch, st, p->line_variant[1]}))) return rc;
+    if ((rc = with_len(p->N[1], LineRun<R, FWD>{&yf, p->n[0], batch, st, p->line_variant[1]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
     if ((rc = with_len(p->N[0], LineRun<R, XMUL>{&x, p->N[1], batch, st, p->line_variant[0]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[1], LineRun<R, INV>{&y, p->n[0], batch, st, p->line_variant[1]}))) return rc;
+    if ((rc = with_len(p->N[1], LineRun<R, INV>{&yi, p->n[0], batch, st, p->line_variant[1]}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
-    if ((rc = with_len(p->N[2], ZRun<R, Tio>{&z, false, batch, st}))) return rc;
+    if ((rc = with_len(p->N[2], ZRun<R, Tio>{&zi, false, batch, st}))) return rc;
     if (mark && (rc = sp_mark(p, st))) return rc;
     return SP_OK;
 }
