@@ -268,11 +268,24 @@ template <class R, int N, int MODE> constexpr int stage_rows() { return MODE == 
 // Two exchange buffers when they fit beside the twiddles and the stage in 110 KB (two CTAs
 // per SM), else one.
 // The y passes of the 32-value plan at 512 (one exchange a transform) trade the second
-// buffer for a third resident CTA (measured: y passes 10 % faster; the x pass, with two
-// transforms a tile, and the 1024 passes are faster with two buffers and two CTAs).
+// buffer for a third resident CTA (measured: y passes 10 % faster; the 1024 passes are
+// faster with two buffers and two CTAs).  So does the FP32 x pass of that plan, whose
+// multiplier rows are then copied into shared memory by cp.async (one stage, refilled for
+// the next tile right after the multiply) instead of being held in 32 registers a thread
+// (measured: x pass 0.224 against 0.235 ms at 256^3; with two multiplier stages, which
+// leave room for two CTAs only, or with the twiddles read from global memory instead of
+// shared memory, it is slower than the register version).
+template <class R, int N, int MODE, class K = R> constexpr bool pipe_mstage()
+{
+    return MODE == XMUL && std::is_same<R, float>::value && N <= 512 && PlanOf<K, N>::E >= 32;
+}
 template <class R, int N, int MODE, class K = R> constexpr bool pipe_third_cta()
 {
-    return PlanOf<K, N>::E >= 32 && MODE != XMUL && N <= 512;
+    return (PlanOf<K, N>::E >= 32 && MODE != XMUL && N <= 512) || pipe_mstage<R, N, MODE, K>();
+}
+template <class R, int N, int MODE, class K = R> constexpr size_t pipe_mstage_bytes()
+{
+    return pipe_mstage<R, N, MODE, K>() ? sizeof(R) * (size_t)(N / 2 + 1) * (1 << lg_default<N>()) : 0;
 }
 template <class R, int N, int MODE, class K = R> constexpr bool pipe_two_buffers()
 {
@@ -287,7 +300,8 @@ template <class R, int N, int MODE, class K = R> constexpr size_t pipe_smem()
     constexpr int B = 1 << lg_default<N>();
     constexpr size_t buf = sizeof(cpx<R>) * (size_t)LayStrided<R>::size(N, B);
     constexpr size_t twb = sizeof(cpx<R>) * tw_entries<K, N>();
-    return twb + (pipe_two_buffers<R, N, MODE, K>() ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B;
+    return twb + (pipe_two_buffers<R, N, MODE, K>() ? 2 : 1) * buf + sizeof(cpx<R>) * (size_t)stage_rows<R, N, MODE>() * B +
+           pipe_mstage_bytes<R, N, MODE, K>();
 }
 
 template <class R, int N, int MODE, class K = R>
@@ -301,10 +315,14 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
     constexpr int NIN = stage_rows<R, N, MODE>();
     constexpr int CH = B * (int)sizeof(cpx<R>) / 16;  // 16-byte chunks per row
     using Lay = LayStrided<R>;
+    constexpr bool MST = pipe_mstage<R, N, MODE, K>();
+    constexpr int MROWS = N / 2 + 1;              // MST: multiplier rows |kx| = 0 .. N/2
+    constexpr int MCH = B * (int)sizeof(R) / 16;  // MST: 16-byte chunks per multiplier row
     // cp.async writes 16-byte chunks: the stage must start on a 16-byte boundary
     static_assert((sizeof(cpx<R>) * tw_entries<K, N>()) % 16 == 0, "twiddle area alignment");
     static_assert((sizeof(cpx<R>) * Lay::size(N, B)) % 16 == 0, "exchange buffer alignment");
     static_assert((B * sizeof(cpx<R>)) % 16 == 0, "stage row alignment");
+    static_assert(!MST || (B * sizeof(R)) % 16 == 0, "multiplier stage alignment");
     const LArgs& a = pa.a;
     const int BUF = Lay::size(N, B);
     constexpr bool DB = pipe_two_buffers<R, N, MODE, K>();
@@ -313,6 +331,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
     cpx<R>* sm0 = tws + tw_entries<K, N>();
     cpx<R>* sm1 = DB ? sm0 + BUF : sm0;
     cpx<R>* stg = sm0 + (DB ? 2 : 1) * BUF;
+    R* mstg = reinterpret_cast<R*>(stg + NIN * B);  // MST: [|kx|][column of the tile]
     const int tid = threadIdx.x, b = tid & (B - 1), t = tid >> LGB;
     const cpx<R>* twg = static_cast<const cpx<R>*>(a.tw);
     if constexpr (MODE != INV) fill_stage_twiddles<R, N, false, K>(tws, twg, tid, blockDim.x);
@@ -346,11 +365,26 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
         }
         cp_async_commit();
     };
+    // MST: the tile's multiplier rows M[|ky|][|kx|][c0 .. c0 + B), |kx| = 0 .. N/2
+    auto issue_m = [&](TileIdx x) {
+        const int xo = a.reverse ? pa.outer - 1 - x.o : x.o;
+        const int ko = xo <= a.No / 2 ? xo : a.No - xo;
+        const char* src = reinterpret_cast<const char*>(static_cast<const R*>(a.M) +
+                                                        (long long)ko * (a.nh_line + 1) * a.ldzM + x.cb * B);
+        for (int q = tid; q < MROWS * MCH; q += blockDim.x) {
+            const int row = q / MCH, ch = q % MCH;
+            cp_async16(reinterpret_cast<char*>(mstg) + (size_t)row * B * sizeof(R) + ch * 16,
+                       src + (long long)row * a.ldzM * (long long)sizeof(R) + ch * 16);
+        }
+    };
     TileIdx cur;
     cur.cb = (int)blockIdx.x % pa.ncb;
     cur.o = ((int)blockIdx.x / pa.ncb) % pa.outer;
     cur.batch = ((int)blockIdx.x / pa.ncb) / pa.outer;
-    if (blockIdx.x < pa.ntiles) issue(cur);
+    if (blockIdx.x < pa.ntiles) {
+        if constexpr (MST) issue_m(cur);  // committed with the rows
+        issue(cur);
+    }
     for (int tile = blockIdx.x; tile < pa.ntiles; tile += gridDim.x) {
         const TileIdx nxt = advance(cur);
         const int batch = cur.batch, o = a.reverse ? pa.outer - 1 - cur.o : cur.o, cb = cur.cb;
@@ -367,7 +401,7 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
             for (int j = 0; j < E; ++j)
                 v[j] = ((j % R0) < R0 / 2) ? stg[first_element<K, N, false>(t, j) * B + b] : czero<R>();
         }
-        constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4;
+        constexpr bool PREFETCH_M = MODE == XMUL && sizeof(R) == 4 && !MST;
         R mv[MODE == XMUL ? E : 1];
         const R* M = static_cast<const R*>(a.M);
         const int ko = o <= a.No / 2 ? o : a.No - o;
@@ -391,12 +425,23 @@ __global__ void __launch_bounds__(line_threads<R, N, lg_default<N>(), K>(),
         if constexpr (MODE == XMUL) {
 #pragma unroll
             for (int j = 0; j < E; ++j) {
-                if constexpr (!PREFETCH_M) {
+                if constexpr (MST) {
+                    const int e = last_element<K, N, false>(t, j);
+                    const int ke = e <= N / 2 ? e : N - e;
+                    mv[j] = cv ? mstg[ke * B + b] : Num<R>::c(0.0);
+                } else if constexpr (!PREFETCH_M) {
                     const int e = last_element<K, N, false>(t, j);
                     const int ke = e <= N / 2 ? e : N - e;
                     mv[j] = cv ? M[(mrow + ke) * a.ldzM + c] : Num<R>::c(0.0);
                 }
                 v[j] = scale(v[j], mv[j]);
+            }
+            if constexpr (MST) {  // every thread has read the stage: refill it for the next tile
+                if (tile + (int)gridDim.x < pa.ntiles) {
+                    __syncthreads();
+                    issue_m(nxt);
+                    cp_async_commit();
+                }
             }
             run_stages<R, N, true, +1, false, K>(v, fresh, fresh == sm0 ? sm1 : sm0, lay, tws, t);
         }
@@ -589,7 +634,11 @@ sp_status launch_line(const LArgs& a, int outer, int batch, cudaStream_t st)
     // (the workspace), and a stage that still leaves two CTAs per SM
     const bool rows_aligned = ((uintptr_t)a.in % 16 == 0) && (a.in_es * sizeof(cpx<R>)) % 16 == 0 &&
                               (a.in_os * sizeof(cpx<R>)) % 16 == 0 && (a.in_bs * sizeof(cpx<R>)) % 16 == 0;
-    if (ab.lgB == lg_default<N>() && psmem <= 110 * 1024 && rows_aligned && (a.ncol + B - 1) / B * B <= a.in_ld) {
+    // the staged multiplier rows are copied in 16-byte chunks as well
+    const bool m_aligned = !pipe_mstage<R, N, MODE, K>() ||
+                           ((uintptr_t)a.M % 16 == 0 && (a.ldzM * sizeof(R)) % 16 == 0 && (a.ncol + B - 1) / B * B <= a.ldzM);
+    if (ab.lgB == lg_default<N>() && psmem <= 110 * 1024 && rows_aligned && m_aligned &&
+        (a.ncol + B - 1) / B * B <= a.in_ld) {
         if ((rc = smem_attr<k3_line<R, N, MODE, K>>(psmem))) return rc;
         static std::atomic<int> per_sm_cached{0};  // resident CTAs per SM (same on every GB300)
         int per_sm = per_sm_cached.load(std::memory_order_relaxed);
