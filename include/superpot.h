@@ -47,13 +47,13 @@ typedef enum {
     SP_MIXED = 2, /* rho, u float64; FFT passes in FP32 (FP32 accumulation)          */
     SP_DF32 = 3   /* rho, u float64; FFT passes and multiplier in double-float: pairs
                      of FP32 values hi + lo (about 48 significant bits) on the FP32
-                     pipes; padded lengths 2n in {64, 128, 192, 256, 384, 512, 1024}  */
+                     pipes; the same lengths as the other precisions                   */
 } sp_precision;
 
 typedef enum {
     SP_OK = 0,
     SP_ERR_INVALID = 1,          /* bad argument (null pointer, bad box, ...)          */
-    SP_ERR_UNSUPPORTED_SIZE = 2, /* n < 2, 2n > 2048, or 2n has a prime factor above 7  */
+    SP_ERR_UNSUPPORTED_SIZE = 2, /* n < 2 or 2n > 2048, or a feature the grid lacks     */
     SP_ERR_OOM = 3,              /* device allocation failed                            */
     SP_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed         */
     SP_ERR_TIMEOUT = 5,          /* a bounded device wait gave up                       */
@@ -67,9 +67,11 @@ typedef void* sp_stream; /* a cudaStream_t */
  * sp_plan_create -- validate the problem and allocate the plan's device memory
  * (Alg. 1 inputs).
  *   out        : receives the plan handle (set to NULL on failure).
- *   n[3]       : grid points per axis, each >= 2 with 2n a product of 2s, 3s, 5s and
- *                7s (the padded FFT lengths, transformed by radix 2/3/4/5/7/8
- *                stages), 2n <= 2048.
+ *   n[3]       : grid points per axis, each >= 2 with 2n <= 2048 (2n: the padded FFT
+ *                lengths; products of 2s, 3s, 5s and 7s are transformed by radix
+ *                2/3/4/5/7/8 stages, any other length by Bluestein's algorithm, a
+ *                circular convolution through power-of-two transforms of length
+ *                M >= 4n - 1).
  *   box_lo/hi  : box faces per axis, hi > lo (the grid spans them inclusively).
  *   padding    : must be 2 (the paper's padding factor, Alg. 1).
  *   gs_w, gs_a : host arrays of gs_terms GS weights/exponents (eq. sin_1_x), copied;
@@ -85,8 +87,10 @@ typedef void* sp_stream; /* a cudaStream_t */
  * per batch element (see sp_plan_workspace_bytes).  Allocated on the current device,
  * stream-ordered from its default memory pool (cudaMallocAsync on a stream of the plan's
  * own, complete when this call returns); sp_plan_create_ex takes a caller's allocator.
- * SP_DF32 plans need every 2n in {64, 128, 192, 256, 384, 512, 1024}
- * (else SP_ERR_UNSUPPORTED_SIZE).
+ * Every precision takes the same lengths: register-resident passes where every padded
+ * length has a compiled plan (2n in {64, 128, 192, 256, 384, 512, 1024}), shared-memory
+ * passes (radix 2..8, 3, 5 and 7 stages, or Bluestein's algorithm) elsewhere.  Bluestein
+ * axes also hold a table of 2n + 3M complex values built on the host and copied here.
  */
 sp_status sp_plan_create(sp_plan* out, const int n[3], const double box_lo[3],
                          const double box_hi[3], int padding, const double* gs_w,

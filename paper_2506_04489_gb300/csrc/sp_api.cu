@@ -31,15 +31,6 @@ sp_status sp_cuda_check(cudaError_t e, const char* what)
                    cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-// Padded lengths the radix-2/3/4/5/7/8 passes can transform: products of 2, 3, 5 and 7.
-static bool smooth2357(int m)
-{
-    if (m < 2) return false;
-    for (int f : {2, 3, 5, 7})
-        while (m % f == 0) m /= f;
-    return m == 1;
-}
-
 sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what)
 {
     *ptr = nullptr;
@@ -127,14 +118,8 @@ extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const doubl
     if (allocator && (!allocator->alloc || !allocator->release))
         return sp_fail(SP_ERR_INVALID, "allocator: both alloc and release must be given");
     for (int ax = 0; ax < 3; ++ax) {
-        if (n[ax] < 2 || !smooth2357(2 * n[ax]) || 2 * n[ax] > kMaxLen)
-            return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
-                           "n[%d] = %d: need n >= 2 and 2n a product of 2s, 3s, 5s and 7s, 2n <= %d", ax,
-                           n[ax], kMaxLen);
-        if (prec == SP_DF32 && !sp_v2_supported(2 * n[ax]))
-            return sp_fail(SP_ERR_UNSUPPORTED_SIZE,
-                           "n[%d] = %d: double-float passes need 2n in {64, 128, 192, 256, 384, 512, 1024}", ax,
-                           n[ax]);
+        if (n[ax] < 2 || 2 * n[ax] > kMaxLen)
+            return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "n[%d] = %d: need n >= 2 and 2n <= %d", ax, n[ax], kMaxLen);
         if (!(isfinite(box_lo[ax]) && isfinite(box_hi[ax]) && box_hi[ax] > box_lo[ax]))
             return sp_fail(SP_ERR_INVALID, "box axis %d: need finite lo < hi", ax);
     }
@@ -163,7 +148,15 @@ extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const doubl
         p->hi[ax] = box_hi[ax];
         p->h[ax] = (box_hi[ax] - box_lo[ax]) / (n[ax] - 1);
         p->L[ax] = n[ax] * p->h[ax];
-        sp_radix_plan(p->N[ax], &p->rp[ax]);
+        // a padded length with a prime factor above 7 has no radix plan: Bluestein's
+        // algorithm, a circular convolution of length M = 2^k >= 2N - 1
+        if (!sp_radix_plan(p->N[ax], &p->rp[ax])) {
+            p->rp[ax].nst = 0;
+            int M = 1;
+            while (M < 2 * p->N[ax] - 1) M *= 2;
+            p->blue_M[ax] = M;
+            sp_radix_plan(M, &p->blue_rp[ax]);
+        }
     }
     p->prec = prec;
     p->max_batch = max_batch;
@@ -235,6 +228,20 @@ extern "C" sp_status sp_plan_create_ex(sp_plan* out, const int n[3], const doubl
         SP_ALLOC(p->d_tw64[ax], sizeof(cpx<double>) * p->N[ax]);
         SP_ALLOC(p->d_tw32[ax], sizeof(cpx<float>) * (p->N[ax] + SP_TW_STAGED_MAX));
         SP_ALLOC(p->d_twdf[ax], sizeof(cpx<df32>) * (p->N[ax] + SP_TW_STAGED_MAX));
+    }
+    for (int ax = 0; ax < 3; ++ax) {  // Bluestein tables: built on the host, copied once
+        if (!p->blue_M[ax]) continue;
+        SP_ALLOC(p->d_blue[ax], sp_bluestein_bytes(p, ax));
+        std::vector<unsigned char> host(sp_bluestein_bytes(p, ax));
+        sp_bluestein_fill(p, ax, host.data());
+        // pageable source: the call returns once the bytes are staged, so host may go
+        const cudaError_t ce = p->mem_st ? cudaMemcpyAsync(p->d_blue[ax], host.data(), host.size(),
+                                                           cudaMemcpyHostToDevice, p->mem_st)
+                                         : cudaMemcpy(p->d_blue[ax], host.data(), host.size(), cudaMemcpyHostToDevice);
+        if ((rc = sp_cuda_check(ce, "Bluestein tables"))) {
+            free_plan(p);
+            return rc;
+        }
     }
     const size_t csize = (prec == SP_FP64 || prec == SP_DF32) ? 16 : 8;
     p->work_bytes = csize * (size_t)max_batch * n[0] * (size_t)p->plane;

@@ -17,6 +17,14 @@ template <class R> SP_HD cpx<R> mk(R a, R b) { cpx<R> c; c.re = a; c.im = b; ret
 // Real and imaginary parts as values (a complex type may store its parts split).
 template <class R> SP_HD R re_of(cpx<R> c) { return c.re; }
 template <class R> SP_HD R im_of(cpx<R> c) { return c.im; }
+// Constants of the arithmetic type (the double-float type specialises it).
+template <class R> struct Num;
+template <> struct Num<float> {
+    static SP_HD float c(double d) { return (float)d; }
+};
+template <> struct Num<double> {
+    static SP_HD double c(double d) { return d; }
+};
 template <class R> SP_HD cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk(a.re + b.re, a.im + b.im); }
 template <class R> SP_HD cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk(a.re - b.re, a.im - b.im); }
 template <class R> SP_HD cpx<R> scale(cpx<R> a, R s) { return mk(a.re * s, a.im * s); }
@@ -40,7 +48,8 @@ template <int S, class R> SP_HD cpx<R> mul_si(cpx<R> a)
 // ---------------------------------------------------------------------------------
 // Small DFTs in registers: X[q] = sum_r u[r] exp(S * 2 pi i r q / R), S = -1 forward,
 // +1 inverse (unnormalised).  Constants are the exact values cos/sin of multiples of
-// 2 pi / R, written as sqrt expressions.
+// 2 pi / R, written as sqrt expressions.  Written with re_of/im_of/mk and Num, so that the
+// same butterflies serve float, double and double-float values.
 // ---------------------------------------------------------------------------------
 template <int S, class R> SP_D void dft2(cpx<R>* u)
 {
@@ -51,11 +60,11 @@ template <int S, class R> SP_D void dft2(cpx<R>* u)
 
 template <int S, class R> SP_D void dft3(cpx<R>* u)
 {
-    const R c = R(-0.5);
-    const R s = R(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    const R c = Num<R>::c(-0.5);
+    const R s = Num<R>::c(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
     cpx<R> a = u[0], b = u[1], d = u[2];
     cpx<R> t = b + d, v = b - d;
-    cpx<R> m = mk(a.re + c * t.re, a.im + c * t.im);
+    cpx<R> m = mk(re_of(a) + c * re_of(t), im_of(a) + c * im_of(t));
     cpx<R> w = mul_si<S>(scale(v, s));
     u[0] = a + t;
     u[1] = m + w;
@@ -75,7 +84,7 @@ template <int S, class R> SP_D void dft4(cpx<R>* u)
 // 8 = 2 x 4: even/odd split, twiddles exp(S 2 pi i q / 8).
 template <int S, class R> SP_D void dft8(cpx<R>* u)
 {
-    const R h = R(0.70710678118654752440084436210484904);  // 1/sqrt(2)
+    const R h = Num<R>::c(0.70710678118654752440084436210484904);  // 1/sqrt(2)
     cpx<R> e[4] = {u[0], u[2], u[4], u[6]};
     cpx<R> o[4] = {u[1], u[3], u[5], u[7]};
     dft4<S>(e);
@@ -114,14 +123,14 @@ template <int S, int P, class R> SP_D void dft_odd(cpx<R>* u, const R* c, const 
     out[0] = sum;
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
-        cpx<R> a = u[0], b = mk(R(0), R(0));
+        cpx<R> a = u[0], b = mk(Num<R>::c(0.0), Num<R>::c(0.0));
 #pragma unroll
         for (int j = 1; j <= H; ++j) {
             const int m = (j * q) % P;
             const R cm = m <= H ? c[m] : c[P - m];
             const R sm = m <= H ? s[m] : -s[P - m];
-            a = mk(a.re + cm * t[j].re, a.im + cm * t[j].im);
-            b = mk(b.re + sm * v[j].re, b.im + sm * v[j].im);
+            a = mk(re_of(a) + cm * re_of(t[j]), im_of(a) + cm * im_of(t[j]));
+            b = mk(re_of(b) + sm * re_of(v[j]), im_of(b) + sm * im_of(v[j]));
         }
         const cpx<R> w = mul_si<S>(b);
         out[q] = a + w;
@@ -134,18 +143,20 @@ template <int S, int P, class R> SP_D void dft_odd(cpx<R>* u, const R* c, const 
 template <int S, class R> SP_D void dft5(cpx<R>* u)
 {
     // cos and sin of 2 pi m / 5, m = 0, 1, 2
-    const R c[3] = {R(1), R(0.309016994374947424102293417182819059), R(-0.809016994374947424102293417182819059)};
-    const R s[3] = {R(0), R(0.951056516295153572116439333379382143), R(0.587785252292473129168705954639072769)};
+    const R c[3] = {Num<R>::c(1.0), Num<R>::c(0.309016994374947424102293417182819059),
+                    Num<R>::c(-0.809016994374947424102293417182819059)};
+    const R s[3] = {Num<R>::c(0.0), Num<R>::c(0.951056516295153572116439333379382143),
+                    Num<R>::c(0.587785252292473129168705954639072769)};
     dft_odd<S, 5>(u, c, s);
 }
 
 template <int S, class R> SP_D void dft7(cpx<R>* u)
 {
     // cos and sin of 2 pi m / 7, m = 0..3
-    const R c[4] = {R(1), R(0.623489801858733530525004884004239811), R(-0.222520933956314404288902564496794759),
-                    R(-0.900968867902419126236102319507445051)};
-    const R s[4] = {R(0), R(0.78183148246802980870844452667405775), R(0.974927912181823607018131682993931217),
-                    R(0.433883739117558120475768332848358755)};
+    const R c[4] = {Num<R>::c(1.0), Num<R>::c(0.623489801858733530525004884004239811),
+                    Num<R>::c(-0.222520933956314404288902564496794759), Num<R>::c(-0.900968867902419126236102319507445051)};
+    const R s[4] = {Num<R>::c(0.0), Num<R>::c(0.78183148246802980870844452667405775),
+                    Num<R>::c(0.974927912181823607018131682993931217), Num<R>::c(0.433883739117558120475768332848358755)};
     dft_odd<S, 7>(u, c, s);
 }
 

@@ -222,6 +222,19 @@ template <int S> __device__ __forceinline__ cpx<df32> mul_si(cpx<df32> a)
     return c;
 }
 
+// a * b and a * conj(b) (the first-generation passes' twiddle products): each part is one
+// fused two-product dot, as in the register engine's twiddle products.
+__device__ __forceinline__ cpx<df32> cmul(cpx<df32> a, cpx<df32> b)
+{
+    const df32 ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+    return mk(df_dot_sub(ar, br, ai, bi), df_dot_add(ar, bi, ai, br));
+}
+__device__ __forceinline__ cpx<df32> cmulc(cpx<df32> a, cpx<df32> b)
+{
+    const df32 ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+    return mk(df_dot_add(ar, br, ai, bi), df_dot_sub(ai, br, ar, bi));
+}
+
 // Renormalise both parts (fast two-sum of hi and lo).
 __device__ __forceinline__ cpx<df32> df_norm_c(cpx<df32> a)
 {

@@ -21,13 +21,7 @@
 #include "sp_df32.cuh"
 
 // ------------------------------------------------------------------ numeric traits
-template <class R> struct Num;
-template <> struct Num<float> {
-    static SP_HD float c(double d) { return (float)d; }
-};
-template <> struct Num<double> {
-    static SP_HD double c(double d) { return d; }
-};
+// (Num<float>, Num<double>: sp_common.cuh)
 template <> struct Num<df32> {
     static SP_HD df32 c(double d) { return df_from_double(d); }
 };

@@ -42,6 +42,13 @@ struct sp_plan_s {
     cpx<float>* d_tw32[3];
     cpx<df32>* d_twdf[3];
     RadixPlan rp[3];
+    // Bluestein axes (2n with a prime factor above 7; rp[ax].nst == 0 there): the circular
+    // convolution length M (a power of two >= 4n - 1), its radix plan, and the device table
+    // [chirp, 2n][filter spectrum, forward, M][filter spectrum, inverse, M][twiddles, M]
+    // of complex values in the plan's arithmetic type; NULL on the other axes
+    int blue_M[3];
+    RadixPlan blue_rp[3];
+    void* d_blue[3];
     // solve workspace: max_batch x n0 x 2n1 x ldz complex (pass precision)
     void* d_work;
     size_t work_bytes;
@@ -101,6 +108,10 @@ sp_status sp_mark(sp_plan p, cudaStream_t st);
 // Record the plan's completion event on `st` after work issued there.
 sp_status sp_record_done(sp_plan p, cudaStream_t st);
 // Device allocation owned by the plan (the caller's allocator, else cudaMalloc).
+// Host-built Bluestein table of one axis (layout above), in the plan's arithmetic type:
+// bytes, and the fill into a host buffer of that size.
+size_t sp_bluestein_bytes(const sp_plan_s* p, int ax);
+void sp_bluestein_fill(const sp_plan_s* p, int ax, void* host);
 sp_status sp_plan_alloc(sp_plan p, void** ptr, size_t bytes, const char* what);
 
 // Thread-local error message helpers (sp_api.cu).

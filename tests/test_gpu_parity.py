@@ -16,11 +16,6 @@ pytestmark = pytest.mark.gpu
 from paper_2506_04489_gb300 import Plan, workloads as W  # noqa: E402
 
 TOL = {"fp64": 1e-12, "df32": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
-V2_LENGTHS = {64, 128, 192, 256, 384, 512, 1024}
-
-
-def v2_case(n):
-    return all(2 * m in V2_LENGTHS for m in n)
 
 
 def _rel(a, b):
@@ -65,6 +60,8 @@ CASES = [
     ((35, 25, 40), (-1, -1, -1.5), (1, 1.5, 1)),   # 2n = 70 = 2 x 5 x 7, 50 = 2 x 5 x 5, 80
     ((80, 80, 80), (-1, -1, -1), (1, 1, 1)),       # 2n = 160 = 8 x 4 x 5
     ((112, 70, 98), (-1, -1, -1), (1, 1, 1)),      # 2n = 224 = 8 x 4 x 7, 140, 196 = 4 x 7 x 7
+    ((11, 13, 17), (-1, -1, -1), (1, 1, 1)),       # 2n = 22, 26, 34: Bluestein on every axis
+    ((22, 16, 61), (-1, -1.5, -1), (1, 1, 2)),     # 2n = 44 = 4 x 11, 32 (radix), 122 = 2 x 61 (Bluestein)
 ]
 
 
@@ -105,8 +102,8 @@ def mixture_density(n, lo, hi, seed):
 @pytest.mark.parametrize("n,lo,hi", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed", "df32"])
 def test_solve_matches_oracle(oracle, n, lo, hi, precision):
-    if precision == "df32" and not v2_case(n):
-        pytest.skip("double-float passes exist for the compiled padded lengths only")
+    # double-float runs the register-resident passes where every padded length has a
+    # compiled plan and the first-generation passes (radix 2 to 8, 3, 5, 7) elsewhere
     rho = mixture_density(n, lo, hi, sum(n))
     _, _, M = oracle_tables(oracle, n, lo, hi)
     ref = oracle.solve(M, rho)
@@ -126,9 +123,8 @@ def test_white_noise_matches_oracle(oracle, n, lo, hi):
     assert _rel(u, ref) <= 1e-12
     u32 = gpu_solve(n, lo, hi, rho, "fp32")
     assert _rel(u32, ref) <= 1e-5
-    if v2_case(n):
-        udf = gpu_solve(n, lo, hi, rho, "df32")
-        assert _rel(udf, ref) <= 1e-12
+    udf = gpu_solve(n, lo, hi, rho, "df32")
+    assert _rel(udf, ref) <= 1e-12
 
 
 def test_unit_box_gaussian_fp64_and_analytic(oracle):
@@ -154,11 +150,9 @@ def test_128_workload_densities(oracle, dens):
         assert _rel(u, ref) <= TOL[precision], precision
 
 
-@pytest.mark.parametrize("n", [(16, 24, 18), (32, 64, 32), (96, 32, 64)])
+@pytest.mark.parametrize("n", [(16, 24, 18), (32, 64, 32), (96, 32, 64), (13, 8, 11)])
 @pytest.mark.parametrize("precision", ["fp64", "df32", "fp32"])
 def test_forward_spectrum_matches_oracle(oracle, n, precision):
-    if precision == "df32" and not v2_case(n):
-        pytest.skip("double-float passes exist for the compiled padded lengths only")
     lo, hi = (-1, -1, -1), (1, 1, 1)
     rho = random_density(n, 7)
     plan = Plan(n, lo, hi, precision=precision)

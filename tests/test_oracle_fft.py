@@ -8,7 +8,9 @@ import numpy as np
 import pytest
 
 LENGTHS = [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 18, 20, 24, 25, 27, 28, 32, 35, 40, 48, 49, 64, 70, 96,
-           128, 140, 160, 192, 224, 256, 384, 512, 1024]
+           128, 140, 160, 192, 224, 256, 384, 512, 1024,
+           # prime factors above 7 (padded lengths 2n of grids such as n = 11, 13, 17, 61, 101)
+           11, 13, 22, 26, 34, 38, 46, 122, 202, 254]
 
 
 def brute_dft(x, sign):
