@@ -225,6 +225,27 @@ sp_status sp_plan_copy_tables(sp_plan plan, double* gs_w, double* gs_a, double* 
                               int axis, double* G, double* H);
 
 /*
+ * sp_bluestein_table -- diagnostic, host only (no device work): the table a plan builds
+ * for an axis whose padded length N = 2n has a prime factor above 7, where the passes
+ * run Bluestein's algorithm (the chirp-z transform: jk = (j^2 + k^2 - (k-j)^2) / 2 turns
+ * the length-N DFT into a convolution, evaluated as a circular convolution of length M,
+ * the smallest power of two >= 2N - 1).  Complex values in the pass type of `prec`
+ * (layout as in sp_forward_spectrum), in this order:
+ *   chirp     c_j = exp(-i pi (j^2 mod 2N) / N), j < N;
+ *   D_fwd     DFT_M of conj(c) placed at m and M - m (m < N, zeros between), divided by M;
+ *   D_inv     the same from c;
+ *   twiddles  exp(-2 pi i q / M), q < M.
+ *   n      : grid points of the axis, 2 <= n <= 1024.
+ *   M      : receives M.
+ *   out    : host buffer, or NULL to query M and the size.
+ *   bytes  : with out NULL receives the table's size in bytes; else gives the buffer's size.
+ * SP_ERR_UNSUPPORTED_SIZE when n is out of range or 2n has no prime factor above 7 (radix
+ * stages serve it); SP_ERR_INVALID for NULL M or bytes, an unknown precision, or a buffer
+ * smaller than the table.
+ */
+sp_status sp_bluestein_table(int n, sp_precision prec, int* M, void* out, size_t* bytes);
+
+/*
  * sp_forward_spectrum -- diagnostic: only the forward half of Alg. 2.  Writes the
  * unnormalised padded DFT of rho, spec[kx][ky][kz] for kx < 2n0, ky < 2n1, kz <= n2,
  * as interleaved complex values of the pass type: float64 pairs (SP_FP64), float32 pairs

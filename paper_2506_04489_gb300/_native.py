@@ -104,6 +104,8 @@ lib.sp_plan_gs_terms.restype = ctypes.c_int
 lib.sp_plan_gs_terms.argtypes = [_vp]
 lib.sp_plan_copy_tables.restype = ctypes.c_int
 lib.sp_plan_copy_tables.argtypes = [_vp, _dp, _dp, _dp, ctypes.c_int, _dp, _dp]
+lib.sp_bluestein_table.restype = ctypes.c_int
+lib.sp_bluestein_table.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _vp, ctypes.POINTER(ctypes.c_size_t)]
 lib.sp_plan_set_timing.restype = ctypes.c_int
 lib.sp_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.sp_plan_pass_times.restype = ctypes.c_int

@@ -80,22 +80,47 @@ size_t csize(sp_precision prec)
     return prec == SP_FP64 || prec == SP_DF32 ? 16 : 8;  // cpx<double>, cpx<df32> / cpx<float>
 }
 
-}  // namespace
+size_t table_bytes(int N, int M, sp_precision prec) { return csize(prec) * ((size_t)N + 3 * (size_t)M); }
 
-size_t sp_bluestein_bytes(const sp_plan_s* p, int ax)
+void fill(int N, int M, sp_precision prec, void* host)
 {
-    return csize(p->prec) * ((size_t)p->N[ax] + 3 * (size_t)p->blue_M[ax]);
-}
-
-void sp_bluestein_fill(const sp_plan_s* p, int ax, void* host)
-{
-    const std::vector<cd> t = tables(p->N[ax], p->blue_M[ax]);
+    const std::vector<cd> t = tables(N, M);
     for (size_t i = 0; i < t.size(); ++i) {
         const double re = t[i].real(), im = t[i].imag();
-        switch (p->prec) {
+        switch (prec) {
             case SP_FP64: static_cast<cpx<double>*>(host)[i] = mk(re, im); break;
             case SP_DF32: static_cast<cpx<df32>*>(host)[i] = mk(df_from_double(re), df_from_double(im)); break;
             default: static_cast<cpx<float>*>(host)[i] = mk((float)re, (float)im); break;
         }
     }
+}
+
+}  // namespace
+
+size_t sp_bluestein_bytes(const sp_plan_s* p, int ax) { return table_bytes(p->N[ax], p->blue_M[ax], p->prec); }
+
+void sp_bluestein_fill(const sp_plan_s* p, int ax, void* host) { fill(p->N[ax], p->blue_M[ax], p->prec, host); }
+
+extern "C" sp_status sp_bluestein_table(int n, sp_precision prec, int* M, void* out, size_t* bytes)
+{
+    sp_clear_error();
+    if (!M || !bytes) return sp_fail(SP_ERR_INVALID, "M and bytes must be non-NULL");
+    if (prec != SP_FP64 && prec != SP_FP32 && prec != SP_MIXED && prec != SP_DF32)
+        return sp_fail(SP_ERR_INVALID, "unknown precision %d", (int)prec);
+    if (n < 2 || n > 1024) return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "n = %d: need 2 <= n <= 1024", n);
+    const int N = 2 * n;
+    RadixPlan rp;
+    if (sp_radix_plan(N, &rp))
+        return sp_fail(SP_ERR_UNSUPPORTED_SIZE, "2n = %d: Bluestein serves 2n <= 2048 with a prime factor above 7", N);
+    int m = 1;
+    while (m < 2 * N - 1) m *= 2;
+    *M = m;
+    const size_t need = table_bytes(N, m, prec);
+    if (!out) {
+        *bytes = need;
+        return SP_OK;
+    }
+    if (*bytes < need) return sp_fail(SP_ERR_INVALID, "buffer of %zu bytes; the table needs %zu", *bytes, need);
+    fill(N, m, prec, out);
+    return SP_OK;
 }
