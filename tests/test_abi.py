@@ -36,7 +36,6 @@ def _create(native, n=(8, 8, 8), lo=(-1,) * 3, hi=(1,) * 3, padding=2, gs=None, 
     return rc, h
 
 
-# 2n must be a product of 2s, 3s, 5s and 7s, at most 2048: 2n = 22, 26, 2, 4096, 22, 2 * 4096
 # any n >= 2 with 2n <= 2048 is accepted (lengths with a prime factor above 7 through
 # Bluestein's algorithm); smaller or larger grids are refused before any allocation
 @pytest.mark.parametrize("n,code", [((1, 8, 8), 2), ((8, 1, 8), 2), ((8, 8, 0), 2), ((8, 8, 2048), 2),
